@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused ISLBM time step on GB300.
+
+Workload (default): the 2-D side-heated cavity at Ra = 1e8, Pr = 0.71 on a
+1024 x 1024 tanh-stretched mesh (a = 1.5), D2Q9 + D2Q5, FP32 population
+storage.  One bench step is one full ISLBM time step of the whole cavity
+(virtual streaming + quadratic interpolation + walls + MRT collision, one fused
+kernel).  The timed region holds exactly K steps; before each timed step a
+256 MB buffer is written to flush the 126 MB L2, and each step is bracketed
+by CUDA events on the solver's stream.  The JSON line reports MLUPS
+(node updates per second / 1e6), the roofline of the step kernel against the
+measured HBM bandwidth, an end-to-end number through the C ABI with host
+buffers, and the FP64 oracle timed on the host cores as a CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ISLBM MLUPS & %HBM roofline; wall time to steady Nu, plain vs mixed/learned"
+WORKLOAD = "2-D side-heated cavity, D2Q9+D2Q5, Ra=1e8, Pr=0.71, 1024x1024 tanh-stretched mesh (a=1.5)"
+BYTES_PER_VALUE = {"fp64": 8, "fp32": 4, "fp16dev": 2, "bf16dev": 2}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16dev": "f16", "bf16dev": "bf16"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--Ra", type=float, default=1e8)
+    ap.add_argument("--mesh", default="tanh", choices=["tanh", "erf", "uniform"])
+    ap.add_argument("--precision", default="fp32", choices=list(BYTES_PER_VALUE))
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def profile_traffic():
+    """ncu DRAM bytes per launch of the step kernel, if the committed summary was
+    taken from the current kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "step2d_fp32_tanh1024.md")
+    src = os.path.join(ROOT, "paper_2509_01099_gb300", "csrc", "islbm_d2.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        vals = {}
+        for line in text.splitlines():
+            if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_sha256")):
+                k, v = line.split(":", 1)
+                vals[k.strip().lstrip("- ")] = v.strip().strip("`")
+        if vals.get("source_sha256") == sha:
+            return float(vals["traffic_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_baseline(n: int, steps: int, mesh: str):
+    """FP64 numpy oracle on the host cores (one thread), a bounded sample of the workload."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+from oracle import islbm_oracle as O
+from synthetic import temperature_noise
+xi = getattr(O, 'mesh_{mesh}')({n}, 1.5) if '{mesh}' != 'uniform' else O.mesh_uniform({n})
+cav = O.Cavity(xi, xi, params=O.Params(Ra=1e8))
+cav.init_fields(temperature_noise(cav.shape, 1e-6, seed=0))
+cav.step(1)
+t = time.perf_counter(); cav.step({steps}); dt = time.perf_counter() - t
+print(json.dumps({{"seconds": dt}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    sec = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+    return {"value": n * n * steps / (sec * 1e6), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} time steps of the {n}x{n} {mesh} cavity (Ra=1e8) by the FP64 "
+                      f"numpy oracle on one host core ({sec:.1f} s)"}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 oracle on the host cores, each step a bounded sample
+    (one time step of a 128 x 128 cavity with the workload's mesh and Ra)."""
+    if rank != 0:
+        return
+    from oracle import islbm_oracle as O
+    from synthetic import temperature_noise
+    n = 128
+    xi = O.mesh_uniform(n) if args.mesh == "uniform" else getattr(O, "mesh_" + args.mesh)(n, 1.5)
+    cav = O.Cavity(xi, xi, params=O.Params(Ra=args.Ra))
+    cav.init_fields(temperature_noise(cav.shape, 1e-6, seed=0))
+    cav.step(max(3, args.warmup))
+    t = time.perf_counter()
+    cav.step(args.steps)
+    sec = time.perf_counter() - t
+    value = n * n * args.steps / (sec * 1e6)
+    sample = f"{args.steps} time steps of a {n}x{n} {args.mesh} cavity (Ra={args.Ra:g}) by the FP64 numpy oracle"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def make_solver(pkg, n, mesh, Ra, precision):
+    """A solver built entirely by the library (its own mesh helpers)."""
+    xi = pkg.islbm_mesh_uniform(n) if mesh == "uniform" else getattr(pkg, "islbm_mesh_" + mesh)(n, 1.5)
+    return pkg.Solver(xi, xi, Ra=Ra, precision=precision)
+
+
+def timed_steps(pkg, solver, steps, warmup, flush, torch):
+    """Device time of `steps` single-step launches, each after an L2 flush."""
+    from synthetic import temperature_noise
+    solver.set_fields(temperature_noise(solver.shape, 1e-6, seed=0))
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush.zero_()
+        solver.step(1)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        solver.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / 1e3
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    from paper_2509_01099_gb300 import build as B
+    if rank == 0:
+        B.build()
+    barrier(world)
+    if world > 1:
+        B.build()
+    import paper_2509_01099_gb300 as pkg
+    from synthetic import temperature_noise
+
+    n = args.n
+    nodes = n * n
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    solver = make_solver(pkg, n, args.mesh, args.Ra, args.precision)
+    info = solver.info
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_dev = timed_steps(pkg, solver, args.steps, args.warmup, flush, torch)
+    clk = clocks.stop()
+    barrier(world)
+    t_dev = max_over_ranks(world, t_dev)
+    red = solver.reduce(check=False)
+
+    ms_per_step = 1e3 * t_dev / args.steps
+    value = world * nodes * args.steps / (t_dev * 1e6)
+    bytes_per_update = 2 * (info.q_flow + info.q_temp) * BYTES_PER_VALUE[args.precision]
+    achieved = bytes_per_update * nodes / (t_dev / args.steps) / 1e9
+    pk = peaks()
+    peak, peak_src = (pk["hbm_gbs"], "measured") if pk else (6800.0, "fallback")
+
+    # ---- end to end through the C ABI with host buffers ----
+    inner = 100
+    pin = lambda: torch.empty(nodes, dtype=torch.float64, pin_memory=True).numpy()
+    hT, hu, hv = pin(), pin(), pin()
+    hT[:] = temperature_noise((n, n), 1e-6, seed=0).ravel()
+    hu[:] = 0.0
+    hv[:] = 0.0
+    e2e_iters = max(3, min(20, args.steps // inner))
+    solver.set_fields(hT, hu, hv)
+    solver.step(inner)
+    solver.reduce(check=False)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_iters):
+        solver.set_fields(hT, hu, hv)        # H2D of the step's inputs (pinned)
+        solver.step(inner)
+        solver.reduce(check=False)           # D2H of the result (Nu, Re, mass, ...)
+    t_e2e = max_over_ranks(world, time.perf_counter() - t0)
+    e2e_value = world * nodes * inner * e2e_iters / (t_e2e * 1e6)
+
+    variants = {}
+    if not args.no_variants:
+        for mesh, prec in (("uniform", "fp32"), ("tanh", "fp16dev"), ("uniform", "fp16dev"),
+                           ("tanh", "bf16dev")):
+            s2 = make_solver(pkg, n, mesh, args.Ra, prec)
+            t2 = timed_steps(pkg, s2, min(args.steps, 500), 10, flush, torch)
+            k = min(args.steps, 500)
+            b2 = 2 * 14 * BYTES_PER_VALUE[prec]
+            variants[f"{mesh}_{prec}"] = {
+                "MLUPS": nodes * k / (t2 * 1e6),
+                "GBps": b2 * nodes / (t2 / k) / 1e9,
+                "ms_per_step": 1e3 * t2 / k}
+            s2.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": WORKLOAD if (n == 1024 and args.mesh == "tanh") else
+                       f"2-D cavity {n}x{n} {args.mesh}, Ra={args.Ra:g}",
+                       "n": n, "mesh": args.mesh, "a": 1.5, "Ra": args.Ra, "Pr": 0.71,
+                       "precision": args.precision, "parallelism": f"replicas{world}",
+                       "l2": "flushed before every timed step (256 MB write)",
+                       "L_lu": info.L, "steps_per_tf": info.steps_per_tf},
+            "wctpdt_s": ms_per_step * 1e-3 * info.steps_per_tf,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": profile_traffic(),
+                         "bytes_per_update": bytes_per_update,
+                         "kernel": "k_step (fused stream+interpolate+walls+collide)"},
+            "e2e": {"value": e2e_value, "unit": "MLUPS",
+                    "h2d_bytes_per_step": 3 * 8 * nodes, "d2h_bytes_per_step": 8 * 16,
+                    "definition": f"per step: set_fields from pinned host T,u,v + {inner} time steps + reduce read back"},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "state_check": {"Nu": red.get("Nu"), "Re": red.get("Re"), "status": red.get("status")},
+            "variants": variants,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(n, 6, args.mesh)
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

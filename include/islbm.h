@@ -1,0 +1,230 @@
+/*
+ * islbm.h -- C ABI of the GB300 interpolation-supplemented lattice Boltzmann
+ * solver for side-heated cavity convection.
+ *
+ * Method: Xu, Zhao, Xu & Jiang, "Interpolation-supplemented lattice Boltzmann
+ * simulation of thermal convection on non-uniform meshes", Int. J. Heat Mass
+ * Transfer (2025).  Section references below are to that paper.
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an islbm_status; ISLBM_OK is 0.  On failure the
+ *     message is available from islbm_last_error(handle) (or
+ *     islbm_last_error(NULL) when there is no handle yet).
+ *   - Grids are stored x fastest: node (x, y[, z]) of a field lives at
+ *     index x + nx*(y + ny*z).  Population arrays are [q][z][y][x].
+ *   - "Host" pointers are caller-owned host memory, read or written before the
+ *     call returns.  "Device" pointers are caller-owned CUDA device memory on
+ *     the device of the handle; the call enqueues work on the handle's stream
+ *     and returns without waiting.
+ *   - The library owns the device memory of a handle (two population buffers,
+ *     the interpolation tables and a small reduction scratch area), allocated
+ *     in islbm_create and freed in islbm_destroy.
+ *   - Calls on one handle are not thread-safe; different handles are
+ *     independent.
+ *   - There is no CPU fallback: without a CUDA device islbm_create returns
+ *     ISLBM_ERR_CUDA.
+ *   - Temperatures are the dimensionless T* = (T - T0)/dT with T0 the mean of
+ *     the wall temperatures (hot wall +1/2, cold wall -1/2).  Velocities are in
+ *     lattice units (l.u. per time step); u* = u / u_f with u_f from
+ *     islbm_info.
+ */
+#ifndef ISLBM_H
+#define ISLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ISLBM_API __attribute__((visibility("default")))
+#else
+#define ISLBM_API
+#endif
+
+typedef struct islbm_solver* islbm_t;
+
+typedef enum {
+  ISLBM_OK = 0,
+  ISLBM_ERR_ARG = 1,           /* invalid argument; nothing was changed            */
+  ISLBM_ERR_CUDA = 2,          /* CUDA error, or no usable GPU                     */
+  ISLBM_ERR_OOM = 3,           /* device allocation failed                         */
+  ISLBM_ERR_DIVERGED = 4,      /* a reduction found a non-finite value             */
+  ISLBM_ERR_NOT_CONVERGED = 5, /* steady state not reached within the step budget  */
+  ISLBM_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                    */
+  ISLBM_ERR_IO = 7             /* checkpoint file missing, short or mismatched     */
+} islbm_status;
+
+/* Lattice pair (Sec. 2.1): D2Q9 flow + D2Q5 temperature, or D3Q19 + D3Q7. */
+typedef enum { ISLBM_D2Q9_D2Q5 = 0, ISLBM_D3Q19_D3Q7 = 1 } islbm_lattice;
+
+/* Storage type of the populations.  Collision and interpolation run in FP64
+ * for ISLBM_FP64 and in FP32 otherwise.  All forms store the deviation from
+ * the rest state, f_i - w_i (flow) and g_i (temperature, T0 = 0); FP16DEV and
+ * BF16DEV store those deviations in 16 bits. */
+typedef enum {
+  ISLBM_FP64 = 0,
+  ISLBM_FP32 = 1,
+  ISLBM_FP16DEV = 2,
+  ISLBM_BF16DEV = 3
+} islbm_precision;
+
+/* Interpolation stencil of the virtual streaming (Sec. 2.2): three nodes
+ * centred on the target node (moved inwards at the walls), or shifted one node
+ * upwind of the streaming direction. */
+typedef enum { ISLBM_STENCIL_CENTRED = 0, ISLBM_STENCIL_UPWIND = 1 } islbm_stencil;
+
+/* Optional parameters.  Fill with islbm_default_params and override.  A rate
+ * <= 0 selects the default:
+ *   s_e = s_eps = s_pi = s_nu, s_q = s_m = 8(2 - s_nu)/(8 - s_nu),
+ *   q_j = 3 - sqrt(3) (implied by the a_T formulas of Sec. 2.1), q_e = q_nu = 1. */
+typedef struct {
+  double Ma;          /* Mach number of the free-fall velocity, Sec. 3 (0.1)    */
+  double T_hot;       /* wall temperatures in T* units (+0.5, -0.5)             */
+  double T_cold;
+  double s_e, s_eps, s_q, s_pi, s_m;   /* flow MRT rates (Sec. 2.1)            */
+  double q_j, q_e, q_nu;               /* temperature MRT rates (Sec. 2.1)     */
+  int stencil;        /* islbm_stencil                                          */
+  int reserved[7];
+} islbm_params;
+
+/* Derived lattice-unit parameters of a handle. */
+typedef struct {
+  int dim;            /* 2 or 3                                                 */
+  int n[3];           /* fluid nodes per axis (n[2] = 1 in 2-D)                 */
+  int q_flow, q_temp; /* 9/5 or 19/7                                            */
+  int uniform;        /* 1 if every axis is the uniform mesh (pure shift)       */
+  int precision;      /* islbm_precision                                        */
+  double L;           /* cavity height in l.u. (Table 1)                        */
+  double u_f;         /* free-fall velocity Ma/sqrt(3) in l.u./step (Sec. 3)    */
+  double nu, alpha;   /* viscosity and diffusivity in lattice units            */
+  double gbeta;       /* g beta in lattice units, dT = 1                        */
+  double s_nu, a_T, omega;
+  double steps_per_tf;   /* time steps per free-fall time, L/u_f (Sec. 3)       */
+  double bytes_per_update; /* algorithmic HBM bytes of one node update          */
+  long long time;     /* steps taken since the last set_* call                  */
+} islbm_info_t;
+
+/* Reductions of the current state (Sec. 3 and Sec. 4), accumulated in FP64. */
+typedef struct {
+  double Nu;          /* <Nu> = sqrt(Ra Pr) <u* T*>_V + 1                        */
+  double Nu_hot;      /* minus the wall average of dT/dx (starred units), hot wall, Eq. (17) */
+  double Nu_cold;     /* the same on the cold wall, Eq. (17)                      */
+  double Nu_middle;   /* line average of sqrt(Ra Pr) u T - dT/dx (starred units) at x = 1/2 (2-D; NaN in 3-D) */
+  double Re;          /* <Re> = sqrt(Ra/Pr) <|u*|>_V                             */
+  double Re_uv;       /* same with sqrt(u*^2 + v*^2) (the printed 3-D form)      */
+  double mass;        /* sum rho W (l.u.^d)                                      */
+  double ke;          /* 1/2 sum |u|^2 W                                         */
+  double max_speed;   /* max |u| / u_f                                           */
+  double nonfinite;   /* number of nodes with a non-finite rho, u or T           */
+  long long time;
+} islbm_reductions;
+
+/* ---- mesh helpers (Sec. 2.3) ------------------------------------------------
+ * Fill xi[0 .. n+1] (host, caller-owned, n+2 doubles) with a mesh in
+ * ghost-node form: xi[1..n] are the fluid nodes, xi[0] and xi[n+1] lie one
+ * lattice unit beyond the first and last fluid node, so the half-way walls sit
+ * at (xi[0]+xi[1])/2 and (xi[n]+xi[n+1])/2.
+ *   uniform: xi_j = (j - 0.5)/n (Eq. (14b)); ghosts at -0.5/n and 1 + 0.5/n.
+ *   erf:     xi_j = (erf[a(j/(n+1) - 1/2)]/erf(a/2) + 1)/2 (Sec. 2.3).
+ *   tanh:    the same form with tanh in place of erf.
+ * Requires n >= 4 and a > 0.  The result is exactly symmetric. */
+ISLBM_API islbm_status islbm_mesh_uniform(int n, double* xi);
+ISLBM_API islbm_status islbm_mesh_erf(int n, double a, double* xi);
+ISLBM_API islbm_status islbm_mesh_tanh(int n, double a, double* xi);
+
+/* Fill *p with the defaults listed at islbm_params. */
+ISLBM_API void islbm_default_params(islbm_params* p);
+
+/* Create a cavity solver (Sec. 2.1-2.3, Sec. 3).
+ *   xi_x, xi_y, xi_z: host meshes in ghost-node form of nx+2, ny+2, nz+2
+ *     doubles (copied).  xi_z = NULL for the 2-D lattice.  All axes must share
+ *     the lattice unit xi[1]-xi[0] (to 1e-9 relative), have equal ghost
+ *     spacing at both ends, and increase strictly.  A mesh whose spacings are
+ *     all one lattice unit is streamed by a pure shift.
+ *   Ra, Pr > 0; lattice: islbm_lattice; precision: islbm_precision.
+ *   opt: NULL for the defaults.
+ *   stream: cudaStream_t to enqueue all work on (NULL = the legacy stream).
+ * The cavity height L (Table 1) sets nu = u_f L sqrt(Pr/Ra),
+ * alpha = u_f L / sqrt(Pr Ra), g beta = u_f^2 / L.  Fails with ISLBM_ERR_ARG
+ * if 1/s_nu <= 1/2 or a_T lies outside its admissible range
+ * (-4 < a_T <= 1 for D2Q5, -6 < a_T <= 1 for D3Q7).
+ * The new solver holds the rest state rho = 1, u = 0, T = 0.  *out receives
+ * the handle (caller owns it; release with islbm_destroy). */
+ISLBM_API islbm_status islbm_create(const double* xi_x, int nx, const double* xi_y, int ny,
+                                    const double* xi_z, int nz, double Ra, double Pr,
+                                    int lattice, int precision, const islbm_params* opt,
+                                    void* stream, islbm_t* out);
+
+/* Release every resource of the handle (synchronises its stream).  NULL is a no-op. */
+ISLBM_API void islbm_destroy(islbm_t h);
+
+/* Last error message of the handle, or of the calling thread when h is NULL. */
+ISLBM_API const char* islbm_last_error(islbm_t h);
+
+/* Derived parameters of the handle (host struct, filled on return). */
+ISLBM_API islbm_status islbm_info(islbm_t h, islbm_info_t* out);
+
+/* Equilibrium initialisation (Sec. 2.1): f = f^eq(rho, u), g = g^eq(T, u),
+ * followed by the local collision.  Host arrays of n_x*n_y[*n_z] doubles; rho
+ * may be NULL (rho = 1), w must be NULL in 2-D.  Resets the step counter. */
+ISLBM_API islbm_status islbm_set_fields(islbm_t h, const double* rho, const double* T,
+                                        const double* u, const double* v, const double* w);
+
+/* As islbm_set_fields with device pointers (asynchronous on the handle's stream). */
+ISLBM_API islbm_status islbm_set_fields_device(islbm_t h, const double* rho, const double* T,
+                                               const double* u, const double* v,
+                                               const double* w);
+
+/* Initialise from full pre-collision populations: host arrays f[q_flow][z][y][x]
+ * and g[q_temp][z][y][x] in FP64, in the velocity order of the paper's
+ * lattices as listed in the library's documentation.  The library collides
+ * them and stores the result.  Resets the step counter. */
+ISLBM_API islbm_status islbm_set_populations(islbm_t h, const double* f, const double* g);
+
+/* Advance n >= 0 ISLBM time steps (Sec. 2.2): virtual streaming with
+ * quadratic interpolation and wall conditions (Sec. 2.3) followed by the
+ * local MRT collisions (Sec. 2.1), one fused kernel per step.  Asynchronous:
+ * returns after enqueueing. */
+ISLBM_API islbm_status islbm_step(islbm_t h, long long n);
+
+/* Macroscopic fields of the current time step (Sec. 2.1): rho, T*, u, v[, w],
+ * each n_x*n_y[*n_z] doubles in host memory.  Any pointer may be NULL; w must
+ * be NULL in 2-D.  Synchronises the stream. */
+ISLBM_API islbm_status islbm_get_fields(islbm_t h, double* rho, double* T, double* u,
+                                        double* v, double* w);
+
+/* As islbm_get_fields into device buffers (asynchronous). */
+ISLBM_API islbm_status islbm_get_fields_device(islbm_t h, double* rho, double* T, double* u,
+                                               double* v, double* w);
+
+/* The stored state: full post-collision populations f+ and g+ of the current
+ * time step (FP64 host arrays, layout as islbm_set_populations).  Synchronises. */
+ISLBM_API islbm_status islbm_get_populations(islbm_t h, double* f, double* g);
+
+/* Nu, Re, mass and kinetic energy of the current time step (Sec. 3 / Sec. 4),
+ * weighted with the midpoint rule of Eq. (18).  Synchronises.  Returns
+ * ISLBM_ERR_DIVERGED (with *out filled) if any node is non-finite. */
+ISLBM_API islbm_status islbm_reduce(islbm_t h, islbm_reductions* out);
+
+/* Convenience views of islbm_reduce. */
+typedef struct { double vol, hot, cold, middle; } islbm_nu;
+ISLBM_API islbm_status islbm_nusselt(islbm_t h, islbm_nu* out);
+ISLBM_API islbm_status islbm_reynolds(islbm_t h, double* re);
+ISLBM_API islbm_status islbm_mass(islbm_t h, double* m);
+
+/* Wait for all work enqueued on the handle. */
+ISLBM_API islbm_status islbm_synchronize(islbm_t h);
+
+/* Checkpoint: write / read the stored populations, the step counter and a
+ * fingerprint of the mesh and parameters.  islbm_load fails with ISLBM_ERR_IO
+ * if the file is short or was written by a handle with another configuration. */
+ISLBM_API islbm_status islbm_save(islbm_t h, const char* path);
+ISLBM_API islbm_status islbm_load(islbm_t h, const char* path);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISLBM_H */

@@ -1,0 +1,14 @@
+"""GB300-native interpolation-supplemented lattice Boltzmann solver (ISLBM).
+
+The compute path is the CUDA library libislbm.so (sm_103a); this package is
+its Python binding.  See include/islbm.h for the C ABI.
+"""
+from .islbm import (EXPORTS, LATTICES, PRECISIONS, STENCILS, IslbmError, Params, Solver,
+                    islbm_create, islbm_default_params, islbm_destroy, islbm_get_fields,
+                    islbm_get_fields_device, islbm_get_populations, islbm_info, islbm_load,
+                    islbm_mass, islbm_mesh_erf, islbm_mesh_tanh, islbm_mesh_uniform,
+                    islbm_nusselt, islbm_reduce, islbm_reynolds, islbm_save, islbm_set_fields,
+                    islbm_set_fields_device, islbm_set_populations, islbm_step,
+                    islbm_synchronize, library_path, load_library)
+
+__all__ = [n for n in dir() if not n.startswith("_")]

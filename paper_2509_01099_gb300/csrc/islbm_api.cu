@@ -1,0 +1,647 @@
+// Host side of the C ABI declared in include/islbm.h.
+//
+// Set-up follows the paper: meshes (Sec. 2.3, Table 1), lattice-unit
+// parameters (Sec. 2.1, Sec. 3), per-axis quadratic Lagrange tables for the
+// virtual streaming (Sec. 2.2, built once in FP64), and the finishing of the
+// Nu / Re reductions (Sec. 3, Sec. 4, Eq. (17), Eq. (18)).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "islbm_internal.h"
+
+using namespace islbm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+islbm_status fail(Solver* s, islbm_status st, const std::string& msg) {
+  if (s) s->err = msg;
+  g_last_error = msg;
+  return st;
+}
+
+islbm_status cuda_fail(Solver* s, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(s, e == cudaErrorMemoryAllocation ? ISLBM_ERR_OOM : ISLBM_ERR_CUDA, m);
+}
+
+#define CK(s, call)                                   \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(s, e_, #call); \
+  } while (0)
+
+// Mirror a mesh so that xi[n+1-j] = 1 - xi[j] holds exactly.
+void make_symmetric(double* xi, int n) {
+  for (int j = (n + 2) / 2; j <= n + 1; ++j) xi[j] = 1.0 - xi[n + 1 - j];
+}
+
+// Lattice coordinates X_j = (xi_j - xi_0)/(xi_1 - xi_0) (1 l.u. = minimal
+// resolution, Table 1); integer to rounding means the uniform mesh.
+std::vector<double> lattice_coords(const double* xi, int n, bool* uniform) {
+  std::vector<double> X(n + 2);
+  const double lu = xi[1] - xi[0];
+  double dev = 0.0;
+  for (int j = 0; j < n + 2; ++j) {
+    X[j] = (xi[j] - xi[0]) / lu;
+    dev = std::fmax(dev, std::fabs(X[j] - std::nearbyint(X[j])));
+  }
+  *uniform = dev < 1e-9;
+  if (*uniform)
+    for (int j = 0; j < n + 2; ++j) X[j] = std::nearbyint(X[j]);
+  return X;
+}
+
+// Per-axis interpolation tables (Sec. 2.2).  For direction c the value at node
+// j is the quadratic Lagrange interpolant through nodes b, b+1, b+2 evaluated
+// at the departure point X_j - c.  A departure point behind a half-way wall
+// (j = 1 with c = +1, j = n with c = -1) is flagged with base -1.
+void build_axis(Axis& a, const double* xi, int n, int stencil) {
+  a.n = n;
+  a.X = lattice_coords(xi, n, &a.uniform);
+  a.W.resize(n);
+  for (int j = 1; j <= n; ++j) a.W[j - 1] = 0.5 * (a.X[j + 1] - a.X[j - 1]);  // Eq. (18)
+  for (int k = 0; k < 2; ++k) {
+    const int c = k == 0 ? +1 : -1;
+    a.base[k].assign(n, -1);
+    a.w[k].assign(3 * n, 0.0);
+    for (int j = 1; j <= n; ++j) {
+      if ((j == 1 && c == +1) || (j == n && c == -1)) continue;
+      int b = stencil == ISLBM_STENCIL_UPWIND ? j - 1 - c : j - 1;
+      b = b < 1 ? 1 : (b > n - 2 ? n - 2 : b);
+      const double d = a.X[j] - c;
+      const double x0 = a.X[b], x1 = a.X[b + 1], x2 = a.X[b + 2];
+      a.base[k][j - 1] = b - 1;
+      a.w[k][3 * (j - 1) + 0] = (d - x1) * (d - x2) / ((x0 - x1) * (x0 - x2));
+      a.w[k][3 * (j - 1) + 1] = (d - x0) * (d - x2) / ((x1 - x0) * (x1 - x2));
+      a.w[k][3 * (j - 1) + 2] = (d - x0) * (d - x1) / ((x2 - x0) * (x2 - x1));
+    }
+  }
+}
+
+islbm_status check_mesh(const double* xi, int n, const char* name, double* lu) {
+  if (!xi) return fail(nullptr, ISLBM_ERR_ARG, std::string(name) + " is NULL");
+  if (n < 4) return fail(nullptr, ISLBM_ERR_ARG, std::string(name) + ": need at least 4 nodes");
+  for (int j = 0; j <= n; ++j)
+    if (!(xi[j + 1] > xi[j]) || !std::isfinite(xi[j + 1]))
+      return fail(nullptr, ISLBM_ERR_ARG, std::string(name) + " is not strictly increasing");
+  const double lo = xi[1] - xi[0], hi = xi[n + 1] - xi[n];
+  if (std::fabs(lo - hi) > 1e-9 * lo)
+    return fail(nullptr, ISLBM_ERR_ARG,
+                std::string(name) + ": ghost spacing differs at the two ends");
+  for (int j = 1; j < n; ++j)
+    if (xi[j + 1] - xi[j] < lo * (1.0 - 1e-9))
+      return fail(nullptr, ISLBM_ERR_ARG,
+                  std::string(name) + ": a fluid spacing is below one lattice unit");
+  *lu = lo;
+  return ISLBM_OK;
+}
+
+// Simple FNV-1a over the configuration, for checkpoints.
+unsigned long long fnv(const void* data, size_t n, unsigned long long h) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 1099511628211ull;
+  return h;
+}
+
+islbm_status finish_reductions(Solver* s, islbm_reductions* out) {
+  const double* r = s->hresult;
+  const Physics& h = s->ph;
+  const double L = h.L, d = s->dim;
+  const double vol = std::pow(L, d), area = std::pow(L, d - 1);
+  const double dT = h.dT;
+  islbm_reductions o;
+  std::memset(&o, 0, sizeof(o));
+  // <Nu> = sqrt(Ra Pr) <u* T*>_V + 1, <Re> = sqrt(Ra/Pr) <|u*|>_V (Sec. 3, Sec. 4)
+  o.Nu = std::sqrt(h.Ra * h.Pr) * r[RED_UT] / (h.u_f * dT * vol) + 1.0;
+  o.Re = std::sqrt(h.Ra / h.Pr) * r[RED_SPEED] / (h.u_f * vol);
+  o.Re_uv = std::sqrt(h.Ra / h.Pr) * r[RED_SPEED_UV] / (h.u_f * vol);
+  o.mass = r[RED_MASS];
+  o.ke = 0.5 * r[RED_U2];
+  // Nu_hot / Nu_cold = -<dT*/dx*> with dT*/dx* = (L/dT) dT/dX by Eq. (17); the
+  // wall-plane sums of T are linear in the node values.
+  const double hot = h.hot_cw * h.T_hot * area + h.hot_c1 * r[RED_HOT1] + h.hot_c2 * r[RED_HOT2];
+  const double cold =
+      h.cold_cw * h.T_cold * area + h.cold_c1 * r[RED_COLD1] + h.cold_c2 * r[RED_COLD2];
+  o.Nu_hot = -hot * L / (dT * area);
+  o.Nu_cold = -cold * L / (dT * area);
+  if (s->dim == 2) {
+    const double conv = std::sqrt(h.Ra * h.Pr) * r[RED_MIDCONV] / (h.u_f * dT);
+    const double cond = L * (r[RED_MIDTR] - r[RED_MIDTL]) * h.mid_inv_dx / dT;
+    o.Nu_middle = (conv - cond) / L;
+  } else {
+    o.Nu_middle = NAN;
+  }
+  o.max_speed = r[RED_MAXSPEED] / h.u_f;
+  o.nonfinite = r[RED_NONFINITE];
+  o.time = s->time;
+  *out = o;
+  if (o.nonfinite > 0 || !std::isfinite(o.Nu) || !std::isfinite(o.mass))
+    return fail(s, ISLBM_ERR_DIVERGED, "non-finite values in the state");
+  return ISLBM_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// mesh helpers
+// ============================================================================
+
+extern "C" islbm_status islbm_mesh_uniform(int n, double* xi) {
+  if (n < 4 || !xi) return fail(nullptr, ISLBM_ERR_ARG, "islbm_mesh_uniform: n >= 4 and xi");
+  for (int j = 0; j <= n + 1; ++j) xi[j] = (j - 0.5) / n;   // Eq. (14b) + ghost nodes
+  make_symmetric(xi, n);
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_mesh_erf(int n, double a, double* xi) {
+  if (n < 4 || !xi || !(a > 0))
+    return fail(nullptr, ISLBM_ERR_ARG, "islbm_mesh_erf: n >= 4, a > 0 and xi");
+  const double den = std::erf(0.5 * a);
+  for (int j = 0; j <= n + 1; ++j)
+    xi[j] = 0.5 * (std::erf(a * (double(j) / (n + 1) - 0.5)) / den + 1.0);
+  make_symmetric(xi, n);
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_mesh_tanh(int n, double a, double* xi) {
+  if (n < 4 || !xi || !(a > 0))
+    return fail(nullptr, ISLBM_ERR_ARG, "islbm_mesh_tanh: n >= 4, a > 0 and xi");
+  const double den = std::tanh(0.5 * a);
+  for (int j = 0; j <= n + 1; ++j)
+    xi[j] = 0.5 * (std::tanh(a * (double(j) / (n + 1) - 0.5)) / den + 1.0);
+  make_symmetric(xi, n);
+  return ISLBM_OK;
+}
+
+extern "C" void islbm_default_params(islbm_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->Ma = 0.1;
+  p->T_hot = 0.5;
+  p->T_cold = -0.5;
+  p->stencil = ISLBM_STENCIL_CENTRED;
+}
+
+// ============================================================================
+// create / destroy
+// ============================================================================
+
+extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* xi_y, int ny,
+                                     const double* xi_z, int nz, double Ra, double Pr,
+                                     int lattice, int precision, const islbm_params* opt,
+                                     void* stream, islbm_t* out) {
+  if (!out) return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: out is NULL");
+  *out = nullptr;
+  if (lattice != ISLBM_D2Q9_D2Q5 && lattice != ISLBM_D3Q19_D3Q7)
+    return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: unknown lattice");
+  if (precision < ISLBM_FP64 || precision > ISLBM_BF16DEV)
+    return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: unknown precision");
+  const int dim = lattice == ISLBM_D2Q9_D2Q5 ? 2 : 3;
+  if ((dim == 2) != (xi_z == nullptr))
+    return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: xi_z must be NULL exactly for the 2-D lattice");
+  if (!(Ra > 0) || !(Pr > 0) || !std::isfinite(Ra) || !std::isfinite(Pr))
+    return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: Ra and Pr must be positive");
+  islbm_params prm;
+  islbm_default_params(&prm);
+  if (opt) prm = *opt;
+  if (!(prm.Ma > 0)) return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: Ma must be positive");
+  if (prm.stencil != ISLBM_STENCIL_CENTRED && prm.stencil != ISLBM_STENCIL_UPWIND)
+    return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: unknown stencil");
+  const double* xis[3] = {xi_x, xi_y, xi_z};
+  const int ns[3] = {nx, ny, dim == 3 ? nz : 1};
+  const char* names[3] = {"xi_x", "xi_y", "xi_z"};
+  double lu[3] = {0, 0, 0};
+  for (int a = 0; a < dim; ++a) {
+    islbm_status st = check_mesh(xis[a], ns[a], names[a], &lu[a]);
+    if (st != ISLBM_OK) return st;
+  }
+  for (int a = 1; a < dim; ++a)
+    if (std::fabs(lu[a] - lu[0]) > 1e-9 * lu[0])
+      return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: axes use different lattice units");
+
+  islbm_solver* s = new (std::nothrow) islbm_solver();
+  if (!s) return fail(nullptr, ISLBM_ERR_OOM, "islbm_create: host allocation");
+  s->dim = dim;
+  s->lattice = lattice;
+  s->precision = precision;
+  s->stencil = prm.stencil;
+  s->stream = static_cast<cudaStream_t>(stream);
+  s->qf = dim == 2 ? 9 : 19;
+  s->qg = dim == 2 ? 5 : 7;
+  s->uniform = true;
+  for (int a = 0; a < 3; ++a) s->n[a] = ns[a];
+  for (int a = 0; a < dim; ++a) {
+    build_axis(s->ax[a], xis[a], ns[a], prm.stencil);
+    s->uniform = s->uniform && s->ax[a].uniform;
+  }
+  s->nodes = (long long)s->n[0] * s->n[1] * s->n[2];
+
+  // ---- physics (Sec. 2.1, Sec. 3, Table 1) ----
+  Physics& h = s->ph;
+  const Axis& ay = s->ax[1];
+  h.Ra = Ra;
+  h.Pr = Pr;
+  h.Ma = prm.Ma;
+  h.L = ay.X[ay.n] - ay.X[1] + 1.0;   // distance between the half-way walls
+  h.u_f = prm.Ma / std::sqrt(3.0);
+  h.nu = h.u_f * h.L * std::sqrt(Pr / Ra);
+  h.alpha = h.u_f * h.L / std::sqrt(Pr * Ra);
+  h.gbeta = h.u_f * h.u_f / h.L;
+  h.T_hot = prm.T_hot;
+  h.T_cold = prm.T_cold;
+  h.T0 = 0.5 * (prm.T_hot + prm.T_cold);
+  h.dT = (prm.T_hot != prm.T_cold) ? prm.T_hot - prm.T_cold : 1.0;
+  h.s_nu = 1.0 / (3.0 * h.nu + 0.5);
+  const double magic = 8.0 * (2.0 - h.s_nu) / (8.0 - h.s_nu);
+  h.s_e = prm.s_e > 0 ? prm.s_e : h.s_nu;
+  h.s_eps = prm.s_eps > 0 ? prm.s_eps : h.s_nu;
+  h.s_pi = prm.s_pi > 0 ? prm.s_pi : h.s_nu;
+  h.s_q = prm.s_q > 0 ? prm.s_q : magic;
+  h.s_m = prm.s_m > 0 ? prm.s_m : magic;
+  h.q_j = prm.q_j > 0 ? prm.q_j : 3.0 - std::sqrt(3.0);
+  h.q_e = prm.q_e > 0 ? prm.q_e : 1.0;
+  h.q_nu = prm.q_nu > 0 ? prm.q_nu : 1.0;
+  if (dim == 2) {
+    h.a_T = 20.0 * std::sqrt(3.0) * h.alpha - 4.0;
+    h.omega = (4.0 + h.a_T) / 10.0;
+    if (!(h.a_T > -4.0 && h.a_T <= 1.0)) {
+      delete s;
+      return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: a_T outside (-4, 1] (diffusivity too large)");
+    }
+  } else {
+    h.a_T = 42.0 * std::sqrt(3.0) * h.alpha - 6.0;
+    h.omega = (6.0 + h.a_T) / 21.0;
+    if (!(h.a_T > -6.0 && h.a_T <= 1.0)) {
+      delete s;
+      return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: a_T outside (-6, 1] (diffusivity too large)");
+    }
+  }
+  // Eq. (17) coefficients with Delta = 1 l.u. and q = (X_2 - X_1)/(X_1 - X_0)
+  const Axis& ax = s->ax[0];
+  const int N = ax.n;
+  {
+    const double q = (ax.X[2] - ax.X[1]) / (ax.X[1] - ax.X[0]);
+    const double den = q * (2 * q + 1);
+    h.hot_cw = -4 * q * (q + 1) / den;
+    h.hot_c1 = (2 * q + 1) * (2 * q + 1) / den;
+    h.hot_c2 = -1.0 / den;
+  }
+  {
+    const double q = (ax.X[N] - ax.X[N - 1]) / (ax.X[N + 1] - ax.X[N]);
+    const double den = q * (2 * q + 1);
+    h.cold_cw = 4 * q * (q + 1) / den;
+    h.cold_c1 = -(2 * q + 1) * (2 * q + 1) / den;
+    h.cold_c2 = 1.0 / den;
+  }
+  if (N % 2 == 0)
+    h.mid_inv_dx = 1.0 / (ax.X[N / 2 + 1] - ax.X[N / 2]);
+  else
+    h.mid_inv_dx = 1.0 / (ax.X[(N + 1) / 2 + 1] - ax.X[(N + 1) / 2 - 1]);
+
+  // ---- device and memory ----
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    delete s;
+    return fail(nullptr, ISLBM_ERR_CUDA, "islbm_create: no CUDA device");
+  }
+  cudaGetDevice(&s->device);
+  s->elem = precision == ISLBM_FP64 ? 8 : (precision == ISLBM_FP32 ? 4 : 2);
+  s->pitch = (s->n[0] + 31) / 32 * 32;
+  s->plane = (long long)s->pitch * s->n[1] * s->n[2];
+  const size_t pop_bytes = (size_t)(s->qf + s->qg) * s->plane * s->elem;
+  const size_t rsize = precision == ISLBM_FP64 ? 8 : 4;
+  size_t tab_bytes = 0;
+  for (int a = 0; a < dim; ++a) {
+    const int n = s->n[a];
+    tab_bytes += 2 * (((size_t)n * 4 + 255) / 256 * 256);
+    tab_bytes += 2 * (((size_t)3 * n * rsize + 255) / 256 * 256);
+    tab_bytes += ((size_t)n * 8 + 255) / 256 * 256;
+  }
+  tab_bytes += 256;
+  s->red_blocks = 4 * 152;
+  auto cleanup = [&](islbm_status st, const std::string& m) {
+    islbm_destroy(s);
+    return fail(nullptr, st, m);
+  };
+  cudaError_t e;
+  for (int b = 0; b < 2; ++b) {
+    e = cudaMalloc(&s->buf[b], pop_bytes);
+    if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: population buffers");
+  }
+  e = cudaMalloc(&s->dtables, tab_bytes);
+  if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: tables");
+  e = cudaMalloc(&s->dscratch, (size_t)s->red_blocks * RED_STRIDE * sizeof(double));
+  if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: reduction scratch");
+  e = cudaMalloc(&s->dresult, RED_STRIDE * sizeof(double));
+  if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: reduction result");
+  e = cudaMallocHost(&s->hresult, RED_STRIDE * sizeof(double));
+  if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: pinned result");
+  // pack the tables on the host and copy once
+  std::vector<char> host(tab_bytes, 0);
+  size_t off = 0;
+  char* dbase = static_cast<char*>(s->dtables);
+  for (int a = 0; a < dim; ++a) {
+    const Axis& A = s->ax[a];
+    const int n = A.n;
+    for (int k = 0; k < 2; ++k) {
+      off = (off + 255) & ~size_t(255);
+      std::memcpy(host.data() + off, A.base[k].data(), (size_t)n * 4);
+      s->dax[a].base[k] = reinterpret_cast<const int*>(dbase + off);
+      off += (size_t)n * 4;
+      off = (off + 255) & ~size_t(255);
+      for (int i = 0; i < 3 * n; ++i) {
+        if (rsize == 8) {
+          double v = A.w[k][i];
+          std::memcpy(host.data() + off + (size_t)i * 8, &v, 8);
+        } else {
+          float v = (float)A.w[k][i];
+          std::memcpy(host.data() + off + (size_t)i * 4, &v, 4);
+        }
+      }
+      s->dax[a].w[k] = dbase + off;
+      off += (size_t)3 * n * rsize;
+    }
+    off = (off + 255) & ~size_t(255);
+    std::memcpy(host.data() + off, A.W.data(), (size_t)n * 8);
+    s->dax[a].W = reinterpret_cast<const double*>(dbase + off);
+    off += (size_t)n * 8;
+  }
+  e = cudaMemcpyAsync(s->dtables, host.data(), tab_bytes, cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) return cleanup(ISLBM_ERR_CUDA, "islbm_create: table upload");
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cleanup(ISLBM_ERR_CUDA, "islbm_create: table upload");
+
+  // configuration fingerprint for checkpoints
+  unsigned long long fp = 1469598103934665603ull;
+  int cfg[6] = {dim, lattice, precision, s->n[0], s->n[1], s->n[2]};
+  fp = fnv(cfg, sizeof(cfg), fp);
+  double phys[4] = {Ra, Pr, prm.Ma, h.L};
+  fp = fnv(phys, sizeof(phys), fp);
+  for (int a = 0; a < dim; ++a) fp = fnv(s->ax[a].X.data(), s->ax[a].X.size() * 8, fp);
+  s->fingerprint = fp;
+
+  // rest state rho = 1, u = 0, T = T0: all deviations vanish
+  for (int b = 0; b < 2; ++b) {
+    e = cudaMemsetAsync(s->buf[b], 0, pop_bytes, s->stream);
+    if (e != cudaSuccess) return cleanup(ISLBM_ERR_CUDA, "islbm_create: memset");
+  }
+  *out = s;
+  return ISLBM_OK;
+}
+
+extern "C" void islbm_destroy(islbm_t s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  for (int b = 0; b < 2; ++b)
+    if (s->buf[b]) cudaFree(s->buf[b]);
+  if (s->dtables) cudaFree(s->dtables);
+  if (s->dscratch) cudaFree(s->dscratch);
+  if (s->dresult) cudaFree(s->dresult);
+  if (s->dfield) cudaFree(s->dfield);
+  if (s->hresult) cudaFreeHost(s->hresult);
+  delete s;
+}
+
+extern "C" const char* islbm_last_error(islbm_t s) {
+  return s ? s->err.c_str() : g_last_error.c_str();
+}
+
+extern "C" islbm_status islbm_info(islbm_t s, islbm_info_t* o) {
+  if (!s || !o) return fail(s, ISLBM_ERR_ARG, "islbm_info: NULL argument");
+  std::memset(o, 0, sizeof(*o));
+  o->dim = s->dim;
+  for (int a = 0; a < 3; ++a) o->n[a] = s->n[a];
+  o->q_flow = s->qf;
+  o->q_temp = s->qg;
+  o->uniform = s->uniform ? 1 : 0;
+  o->precision = s->precision;
+  const Physics& h = s->ph;
+  o->L = h.L;
+  o->u_f = h.u_f;
+  o->nu = h.nu;
+  o->alpha = h.alpha;
+  o->gbeta = h.gbeta;
+  o->s_nu = h.s_nu;
+  o->a_T = h.a_T;
+  o->omega = h.omega;
+  o->steps_per_tf = h.L / h.u_f;
+  o->bytes_per_update = 2.0 * (s->qf + s->qg) * (double)s->elem;
+  o->time = s->time;
+  return ISLBM_OK;
+}
+
+// ============================================================================
+// state in / out
+// ============================================================================
+
+static islbm_status ensure_field_buffer(Solver* s) {
+  if (s->dfield) return ISLBM_OK;
+  const size_t q = (size_t)(s->qf + s->qg);
+  const size_t need = std::max<size_t>(5, q) * (size_t)s->nodes * sizeof(double);
+  cudaError_t e = cudaMalloc(&s->dfield, need);
+  if (e != cudaSuccess) return cuda_fail(s, e, "field staging buffer");
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_set_fields_device(islbm_t s, const double* rho, const double* T,
+                                                const double* u, const double* v,
+                                                const double* w) {
+  if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_set_fields: NULL handle");
+  if (!T) return fail(s, ISLBM_ERR_ARG, "islbm_set_fields: T is required");
+  if (s->dim == 2 && w) return fail(s, ISLBM_ERR_ARG, "islbm_set_fields: w must be NULL in 2-D");
+  CK(s, launch_init_fields(*s, rho, T, u, v, w));
+  s->time = 0;
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_set_fields(islbm_t s, const double* rho, const double* T,
+                                         const double* u, const double* v, const double* w) {
+  if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_set_fields: NULL handle");
+  if (!T) return fail(s, ISLBM_ERR_ARG, "islbm_set_fields: T is required");
+  if (s->dim == 2 && w) return fail(s, ISLBM_ERR_ARG, "islbm_set_fields: w must be NULL in 2-D");
+  islbm_status st = ensure_field_buffer(s);
+  if (st != ISLBM_OK) return st;
+  const size_t n = (size_t)s->nodes;
+  const double* src[5] = {rho, T, u, v, w};
+  double* dst[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  for (int k = 0; k < 5; ++k) {
+    if (!src[k]) continue;
+    dst[k] = s->dfield + k * n;
+    CK(s, cudaMemcpyAsync(dst[k], src[k], n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  }
+  CK(s, launch_init_fields(*s, dst[0], dst[1], dst[2], dst[3], dst[4]));
+  CK(s, cudaStreamSynchronize(s->stream));
+  s->time = 0;
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_set_populations(islbm_t s, const double* f, const double* g) {
+  if (!s || !f || !g) return fail(s, ISLBM_ERR_ARG, "islbm_set_populations: NULL argument");
+  islbm_status st = ensure_field_buffer(s);
+  if (st != ISLBM_OK) return st;
+  const size_t n = (size_t)s->nodes;
+  double* df = s->dfield;
+  double* dg = s->dfield + (size_t)s->qf * n;
+  CK(s, cudaMemcpyAsync(df, f, (size_t)s->qf * n * 8, cudaMemcpyHostToDevice, s->stream));
+  CK(s, cudaMemcpyAsync(dg, g, (size_t)s->qg * n * 8, cudaMemcpyHostToDevice, s->stream));
+  CK(s, launch_init_populations(*s, df, dg));
+  CK(s, cudaStreamSynchronize(s->stream));
+  s->time = 0;
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_step(islbm_t s, long long n) {
+  if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_step: NULL handle");
+  if (n < 0) return fail(s, ISLBM_ERR_ARG, "islbm_step: negative step count");
+  for (long long k = 0; k < n; ++k) {
+    CK(s, launch_step(*s));
+    ++s->time;
+  }
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_get_fields_device(islbm_t s, double* rho, double* T, double* u,
+                                                double* v, double* w) {
+  if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_get_fields: NULL handle");
+  if (s->dim == 2 && w) return fail(s, ISLBM_ERR_ARG, "islbm_get_fields: w must be NULL in 2-D");
+  CK(s, launch_fields(*s, rho, T, u, v, w));
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_get_fields(islbm_t s, double* rho, double* T, double* u,
+                                         double* v, double* w) {
+  if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_get_fields: NULL handle");
+  if (s->dim == 2 && w) return fail(s, ISLBM_ERR_ARG, "islbm_get_fields: w must be NULL in 2-D");
+  islbm_status st = ensure_field_buffer(s);
+  if (st != ISLBM_OK) return st;
+  const size_t n = (size_t)s->nodes;
+  double* dst[5] = {rho, T, u, v, w};
+  double* dev[5];
+  for (int k = 0; k < 5; ++k) dev[k] = dst[k] ? s->dfield + k * n : nullptr;
+  CK(s, launch_fields(*s, dev[0], dev[1], dev[2], dev[3], dev[4]));
+  for (int k = 0; k < 5; ++k)
+    if (dst[k])
+      CK(s, cudaMemcpyAsync(dst[k], dev[k], n * 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_get_populations(islbm_t s, double* f, double* g) {
+  if (!s || !f || !g) return fail(s, ISLBM_ERR_ARG, "islbm_get_populations: NULL argument");
+  islbm_status st = ensure_field_buffer(s);
+  if (st != ISLBM_OK) return st;
+  const size_t n = (size_t)s->nodes;
+  double* df = s->dfield;
+  double* dg = s->dfield + (size_t)s->qf * n;
+  CK(s, launch_populations(*s, df, dg));
+  CK(s, cudaMemcpyAsync(f, df, (size_t)s->qf * n * 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaMemcpyAsync(g, dg, (size_t)s->qg * n * 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_reduce(islbm_t s, islbm_reductions* out) {
+  if (!s || !out) return fail(s, ISLBM_ERR_ARG, "islbm_reduce: NULL argument");
+  CK(s, launch_reduce(*s));
+  CK(s, cudaMemcpyAsync(s->hresult, s->dresult, RED_STRIDE * sizeof(double),
+                        cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return finish_reductions(s, out);
+}
+
+extern "C" islbm_status islbm_nusselt(islbm_t s, islbm_nu* out) {
+  if (!out) return fail(s, ISLBM_ERR_ARG, "islbm_nusselt: NULL argument");
+  islbm_reductions r;
+  islbm_status st = islbm_reduce(s, &r);
+  out->vol = r.Nu;
+  out->hot = r.Nu_hot;
+  out->cold = r.Nu_cold;
+  out->middle = r.Nu_middle;
+  return st;
+}
+
+extern "C" islbm_status islbm_reynolds(islbm_t s, double* re) {
+  if (!re) return fail(s, ISLBM_ERR_ARG, "islbm_reynolds: NULL argument");
+  islbm_reductions r;
+  islbm_status st = islbm_reduce(s, &r);
+  *re = r.Re;
+  return st;
+}
+
+extern "C" islbm_status islbm_mass(islbm_t s, double* m) {
+  if (!m) return fail(s, ISLBM_ERR_ARG, "islbm_mass: NULL argument");
+  islbm_reductions r;
+  islbm_status st = islbm_reduce(s, &r);
+  *m = r.mass;
+  return st;
+}
+
+extern "C" islbm_status islbm_synchronize(islbm_t s) {
+  if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_synchronize: NULL handle");
+  CK(s, cudaStreamSynchronize(s->stream));
+  return ISLBM_OK;
+}
+
+// ============================================================================
+// checkpoints
+// ============================================================================
+
+namespace {
+struct CkptHeader {
+  char magic[8];
+  unsigned long long fingerprint;
+  long long time;
+  long long bytes;
+};
+}  // namespace
+
+extern "C" islbm_status islbm_save(islbm_t s, const char* path) {
+  if (!s || !path) return fail(s, ISLBM_ERR_ARG, "islbm_save: NULL argument");
+  const size_t bytes = (size_t)(s->qf + s->qg) * s->plane * s->elem;
+  std::vector<char> host(bytes);
+  CK(s, cudaMemcpyAsync(host.data(), s->buf[s->cur], bytes, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return fail(s, ISLBM_ERR_IO, std::string("islbm_save: cannot open ") + path);
+  CkptHeader hd;
+  std::memcpy(hd.magic, "ISLBMCK1", 8);
+  hd.fingerprint = s->fingerprint;
+  hd.time = s->time;
+  hd.bytes = (long long)bytes;
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1 && std::fwrite(host.data(), 1, bytes, fp) == bytes;
+  ok = (std::fclose(fp) == 0) && ok;
+  if (!ok) return fail(s, ISLBM_ERR_IO, std::string("islbm_save: short write to ") + path);
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_load(islbm_t s, const char* path) {
+  if (!s || !path) return fail(s, ISLBM_ERR_ARG, "islbm_load: NULL argument");
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(s, ISLBM_ERR_IO, std::string("islbm_load: cannot open ") + path);
+  CkptHeader hd;
+  const size_t bytes = (size_t)(s->qf + s->qg) * s->plane * s->elem;
+  if (std::fread(&hd, sizeof(hd), 1, fp) != 1 || std::memcmp(hd.magic, "ISLBMCK1", 8) != 0) {
+    std::fclose(fp);
+    return fail(s, ISLBM_ERR_IO, "islbm_load: not a checkpoint");
+  }
+  if (hd.fingerprint != s->fingerprint || hd.bytes != (long long)bytes) {
+    std::fclose(fp);
+    return fail(s, ISLBM_ERR_IO, "islbm_load: checkpoint of another configuration");
+  }
+  std::vector<char> host(bytes);
+  const bool ok = std::fread(host.data(), 1, bytes, fp) == bytes;
+  std::fclose(fp);
+  if (!ok) return fail(s, ISLBM_ERR_IO, "islbm_load: truncated checkpoint");
+  CK(s, cudaMemcpyAsync(s->buf[s->cur], host.data(), bytes, cudaMemcpyHostToDevice, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  s->time = hd.time;
+  return ISLBM_OK;
+}

@@ -1,0 +1,548 @@
+// 2-D kernels: D2Q9 flow + D2Q5 temperature populations (Sec. 2.1 - 2.3).
+//
+// Storage: one plane per population, [q][y][x] with a padded x pitch; planes
+// 0..8 hold the flow populations, 9..13 the temperature populations, in the
+// velocity order
+//   D2Q9: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+//   D2Q5: (0,0) (1,0) (0,1) (-1,0) (0,-1).
+// The stored state of time t is the post-collision deviation f_i^+ - w_i
+// (g_i^+ - t_i T0).  One step therefore pulls the post-collision values
+// through the virtual streaming + quadratic interpolation (Sec. 2.2) or the
+// wall rules (Sec. 2.3), forms the macroscopic moments and collides (Sec. 2.1),
+// which is the paper's collide -> stream -> interpolate cycle with the state
+// stored after the collision instead of before it.
+#include <cstdint>
+
+#include "islbm_internal.h"
+#include "islbm_store.cuh"
+
+namespace islbm {
+namespace {
+
+template <typename R>
+struct P2 {
+  int nx, ny, pitch;
+  long long plane;
+  const int* bx[2];
+  const R* wx[2];
+  const int* by[2];
+  const R* wy[2];
+  R gbeta, T0, s_e, s_eps, s_q, s_nu, q_j, q_e, q_nu, a_T;
+  R abb_hot, abb_cold;  // omega (T_w - T0) of the anti-bounce-back rule
+};
+
+// Rest weights w_i of the D2Q9 populations.
+template <typename R>
+__device__ __forceinline__ R wrest(int i) {
+  return i == 0 ? R(4.0 / 9.0) : (i < 5 ? R(1.0 / 9.0) : R(1.0 / 36.0));
+}
+
+// MRT collision of one node in deviation form (Sec. 2.1).
+//   m = M f with the Lallemand-Luo rows (rho, e, eps, jx, qx, jy, qy, pxx, pxy);
+//   m+ = m - S (m - m_eq) + (I - S/2) M F~ with the printed m_eq and M F~;
+//   f+ = f + M^-1 (m+ - m), M^-1 = M^T diag(1/|row_k|^2).
+//   g: n = N g with rows (T, jx, jy, -4+5|c|^2, cx^2-cy^2), n+ = n - Q (n - n_eq).
+// The buoyancy F = rho g beta (T - T0) acts along +y; u = (sum e f + F/2)/rho.
+// Returns rho, u and T of the pre-collision state.
+template <typename R>
+__device__ __forceinline__ void collide(R (&f)[9], R (&g)[5], const P2<R>& p, R& rho_o,
+                                        R& ux_o, R& uy_o, R& T_o) {
+  const R drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const R rho = R(1) + drho;
+  const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  const R jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+  const R Tr = (g[0] + g[1]) + (g[2] + g[3]) + g[4];  // T - T0
+  const R T = Tr + p.T0;
+  const R Fy = rho * p.gbeta * Tr;
+  const R inv = R(1) / rho;
+  const R ux = jx * inv;
+  const R uy = (jy + R(0.5) * Fy) * inv;
+  const R ux2 = ux * ux, uy2 = uy * uy;
+  const R rusq = rho * (ux2 + uy2);
+  const R uF = uy * Fy;
+
+  const R sax = (f[1] + f[2]) + (f[3] + f[4]);
+  const R sdg = (f[5] + f[6]) + (f[7] + f[8]);
+  const R m1 = R(-4) * f[0] - sax + R(2) * sdg;
+  const R m2 = R(4) * f[0] - R(2) * sax + sdg;
+  const R m4 = R(-2) * (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  const R m6 = R(-2) * (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+  const R m7 = (f[1] + f[3]) - (f[2] + f[4]);
+  const R m8 = (f[5] + f[7]) - (f[6] + f[8]);
+
+  // moment increments; the deviation form moves M w = (1,-2,1,0,...) into m_eq
+  const R dm1 = -p.s_e * (m1 + R(2) * drho - R(3) * rusq) + (R(1) - R(0.5) * p.s_e) * R(6) * uF;
+  const R dm2 = -p.s_eps * (m2 - drho + R(3) * rusq) - (R(1) - R(0.5) * p.s_eps) * R(6) * uF;
+  const R dm4 = -p.s_q * (m4 + rho * ux);
+  const R dm5 = Fy;  // j_y gains exactly F_y (independent of s_j)
+  const R dm6 = -p.s_q * (m6 + rho * uy) - (R(1) - R(0.5) * p.s_q) * Fy;
+  const R dm7 = -p.s_nu * (m7 - rho * (ux2 - uy2)) - (R(1) - R(0.5) * p.s_nu) * R(2) * uF;
+  const R dm8 = -p.s_nu * (m8 - rho * ux * uy) + (R(1) - R(0.5) * p.s_nu) * ux * Fy;
+
+  const R a1 = dm1 * R(1.0 / 36.0), a2 = dm2 * R(1.0 / 36.0), a4 = dm4 * R(1.0 / 12.0);
+  const R a5 = dm5 * R(1.0 / 6.0), a6 = dm6 * R(1.0 / 12.0);
+  const R a7 = dm7 * R(0.25), a8 = dm8 * R(0.25);
+  const R cax = -a1 - R(2) * a2;
+  const R cdg = R(2) * a1 + a2;
+  f[0] += R(4) * (a2 - a1);
+  f[1] += cax - R(2) * a4 + a7;
+  f[3] += cax + R(2) * a4 + a7;
+  f[2] += cax + a5 - R(2) * a6 - a7;
+  f[4] += cax - a5 + R(2) * a6 - a7;
+  f[5] += cdg + a4 + a5 + a6 + a8;
+  f[6] += cdg - a4 + a5 + a6 - a8;
+  f[7] += cdg - a4 - a5 - a6 + a8;
+  f[8] += cdg + a4 - a5 - a6 - a8;
+
+  const R n1 = g[1] - g[3], n2 = g[2] - g[4];
+  const R n3 = R(-4) * g[0] + (g[1] + g[2]) + (g[3] + g[4]);
+  const R n4 = (g[1] + g[3]) - (g[2] + g[4]);
+  const R b1 = R(-0.5) * p.q_j * (n1 - ux * T);
+  const R b2 = R(-0.5) * p.q_j * (n2 - uy * T);
+  const R b3 = R(-0.05) * p.q_e * (n3 - p.a_T * Tr);
+  const R b4 = R(-0.25) * p.q_nu * n4;
+  g[0] += R(-4) * b3;
+  g[1] += b1 + b3 + b4;
+  g[3] += -b1 + b3 + b4;
+  g[2] += b2 + b3 - b4;
+  g[4] += -b2 + b3 - b4;
+
+  rho_o = rho;
+  ux_o = ux;
+  uy_o = uy;
+  T_o = T;
+}
+
+// Interpolated pull of one population (Sec. 2.2): the value at node (x, y) is
+// the tensor-product quadratic Lagrange interpolant of the post-collision
+// values at the departure point (X_x - cx, Y_y - cy).  On the uniform mesh the
+// interpolant is a pure shift.
+template <typename S, typename R, int CX, int CY, bool UNI>
+__device__ __forceinline__ R pull(const S* __restrict__ pl, int x, int y, const P2<R>& p) {
+  using St = Store<S>;
+  if (CX == 0 && CY == 0) return St::ld(pl + (size_t)y * p.pitch + x);
+  if (UNI) return St::ld(pl + (size_t)(y - CY) * p.pitch + (x - CX));
+  if (CY == 0) {
+    constexpr int k = CX > 0 ? 0 : 1;
+    const int b = __ldg(p.bx[k] + x);
+    const R* w = p.wx[k] + 3 * x;
+    const S* r = pl + (size_t)y * p.pitch + b;
+    return __ldg(w) * St::ld(r) + __ldg(w + 1) * St::ld(r + 1) + __ldg(w + 2) * St::ld(r + 2);
+  }
+  if (CX == 0) {
+    constexpr int k = CY > 0 ? 0 : 1;
+    const int b = __ldg(p.by[k] + y);
+    const R* w = p.wy[k] + 3 * y;
+    const S* r = pl + (size_t)b * p.pitch + x;
+    return __ldg(w) * St::ld(r) + __ldg(w + 1) * St::ld(r + p.pitch) +
+           __ldg(w + 2) * St::ld(r + 2 * (size_t)p.pitch);
+  }
+  constexpr int kx = CX > 0 ? 0 : 1;
+  constexpr int ky = CY > 0 ? 0 : 1;
+  const int bx = __ldg(p.bx[kx] + x);
+  const int by = __ldg(p.by[ky] + y);
+  const R* wx = p.wx[kx] + 3 * x;
+  const R* wy = p.wy[ky] + 3 * y;
+  const R wx0 = __ldg(wx), wx1 = __ldg(wx + 1), wx2 = __ldg(wx + 2);
+  R acc = R(0);
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const S* r = pl + (size_t)(by + l) * p.pitch + bx;
+    acc += __ldg(wy + l) * (wx0 * St::ld(r) + wx1 * St::ld(r + 1) + wx2 * St::ld(r + 2));
+  }
+  return acc;
+}
+
+template <typename S, bool UNI>
+__global__ void __launch_bounds__(256)
+    k_step(const S* __restrict__ fin, S* __restrict__ fout, P2<typename Store<S>::R> p) {
+  using R = typename Store<S>::R;
+  using St = Store<S>;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const size_t idx = (size_t)y * p.pitch + x;
+  const long long P = p.plane;
+  // departure point behind the west / east / south / north wall
+  const bool wW = (x == 0), wE = (x == p.nx - 1), wS = (y == 0), wN = (y == p.ny - 1);
+  R f[9], g[5];
+  // flow: half-way bounce-back f_i = f_ibar^+ at the wall (Sec. 2.3)
+  f[0] = St::ld(fin + idx);
+  f[1] = wW ? St::ld(fin + 3 * P + idx) : pull<S, R, 1, 0, UNI>(fin + 1 * P, x, y, p);
+  f[2] = wS ? St::ld(fin + 4 * P + idx) : pull<S, R, 0, 1, UNI>(fin + 2 * P, x, y, p);
+  f[3] = wE ? St::ld(fin + 1 * P + idx) : pull<S, R, -1, 0, UNI>(fin + 3 * P, x, y, p);
+  f[4] = wN ? St::ld(fin + 2 * P + idx) : pull<S, R, 0, -1, UNI>(fin + 4 * P, x, y, p);
+  f[5] = (wW || wS) ? St::ld(fin + 7 * P + idx) : pull<S, R, 1, 1, UNI>(fin + 5 * P, x, y, p);
+  f[6] = (wE || wS) ? St::ld(fin + 8 * P + idx) : pull<S, R, -1, 1, UNI>(fin + 6 * P, x, y, p);
+  f[7] = (wE || wN) ? St::ld(fin + 5 * P + idx) : pull<S, R, -1, -1, UNI>(fin + 7 * P, x, y, p);
+  f[8] = (wW || wN) ? St::ld(fin + 6 * P + idx) : pull<S, R, 1, -1, UNI>(fin + 8 * P, x, y, p);
+  // temperature: anti-bounce-back on the isothermal x-walls, bounce-back on the
+  // adiabatic y-walls (Sec. 2.3)
+  const S* gin = fin + 9 * P;
+  g[0] = St::ld(gin + idx);
+  g[1] = wW ? p.abb_hot - St::ld(gin + 3 * P + idx) : pull<S, R, 1, 0, UNI>(gin + 1 * P, x, y, p);
+  g[2] = wS ? St::ld(gin + 4 * P + idx) : pull<S, R, 0, 1, UNI>(gin + 2 * P, x, y, p);
+  g[3] = wE ? p.abb_cold - St::ld(gin + 1 * P + idx) : pull<S, R, -1, 0, UNI>(gin + 3 * P, x, y, p);
+  g[4] = wN ? St::ld(gin + 2 * P + idx) : pull<S, R, 0, -1, UNI>(gin + 4 * P, x, y, p);
+
+  R rho, ux, uy, T;
+  collide(f, g, p, rho, ux, uy, T);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) St::st(fout + i * P + idx, f[i]);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) St::st(fout + (9 + i) * P + idx, g[i]);
+}
+
+// Equilibrium (Sec. 2.1) of given fields, then the collision.  The flow
+// equilibrium is the second-order Hermite form w_i rho (1 + 3 e.u + 9/2 (e.u)^2
+// - 3/2 u^2), which has exactly the printed moments; the temperature
+// equilibrium is N^-1 n_eq: g_0 = t_0 T, g_i = t_i T + (e_i.u) T / 2 with
+// t_0 = (1 - a_T)/5, t_i = (4 + a_T)/20.
+template <typename S>
+__global__ void k_init_fields(S* __restrict__ fout, P2<typename Store<S>::R> p,
+                              const double* __restrict__ rho_in, const double* __restrict__ T_in,
+                              const double* __restrict__ u_in, const double* __restrict__ v_in) {
+  using R = typename Store<S>::R;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const size_t node = (size_t)y * p.nx + x;
+  const R rho = rho_in ? R(rho_in[node]) : R(1);
+  const R T = R(T_in[node]);
+  const R ux = u_in ? R(u_in[node]) : R(0);
+  const R uy = v_in ? R(v_in[node]) : R(0);
+  const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const R usq = ux * ux + uy * uy;
+  R f[9], g[5];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const R eu = R(ex[i]) * ux + R(ey[i]) * uy;
+    f[i] = wrest<R>(i) * (rho * (R(1) + R(3) * eu + R(4.5) * eu * eu - R(1.5) * usq) - R(1));
+  }
+  const R t0 = (R(1) - p.a_T) * R(0.2), ti = (R(4) + p.a_T) * R(0.05);
+  const R Tr = T - p.T0;
+  g[0] = t0 * Tr;
+#pragma unroll
+  for (int i = 1; i < 5; ++i) g[i] = ti * Tr + R(0.5) * (R(ex[i]) * ux + R(ey[i]) * uy) * T;
+  R r_, a_, b_, c_;
+  collide(f, g, p, r_, a_, b_, c_);
+  const size_t idx = (size_t)y * p.pitch + x;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Store<S>::st(fout + i * p.plane + idx, f[i]);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) Store<S>::st(fout + (9 + i) * p.plane + idx, g[i]);
+}
+
+// Full FP64 pre-collision populations ([q][node]) -> deviations -> collision.
+template <typename S>
+__global__ void k_init_pops(S* __restrict__ fout, P2<typename Store<S>::R> p,
+                            const double* __restrict__ fin, const double* __restrict__ gin) {
+  using R = typename Store<S>::R;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const size_t nodes = (size_t)p.nx * p.ny;
+  const size_t node = (size_t)y * p.nx + x;
+  const R t0 = (R(1) - p.a_T) * R(0.2), ti = (R(4) + p.a_T) * R(0.05);
+  R f[9], g[5];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f[i] = R(fin[i * nodes + node] - wrest<double>(i));
+#pragma unroll
+  for (int i = 0; i < 5; ++i) g[i] = R(gin[i * nodes + node]) - (i == 0 ? t0 : ti) * p.T0;
+  R r_, a_, b_, c_;
+  collide(f, g, p, r_, a_, b_, c_);
+  const size_t idx = (size_t)y * p.pitch + x;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Store<S>::st(fout + i * p.plane + idx, f[i]);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) Store<S>::st(fout + (9 + i) * p.plane + idx, g[i]);
+}
+
+// Macroscopic state of a node from the stored post-collision deviations, in
+// FP64: rho and T are collision invariants; the collision adds F to the
+// momentum, so u = (sum e f^+ - F/2)/rho.
+struct NodeState {
+  double rho, ux, uy, T;
+};
+
+template <typename S>
+__device__ __forceinline__ NodeState node_state(const S* __restrict__ s, size_t idx,
+                                                long long P, double gbeta, double T0) {
+  double f[9], g[5];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f[i] = (double)Store<S>::ld(s + i * P + idx);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) g[i] = (double)Store<S>::ld(s + (9 + i) * P + idx);
+  NodeState n;
+  const double drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  n.rho = 1.0 + drho;
+  const double jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  const double jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+  const double Tr = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
+  n.T = Tr + T0;
+  const double Fy = n.rho * gbeta * Tr;
+  n.ux = jx / n.rho;
+  n.uy = (jy - 0.5 * Fy) / n.rho;
+  return n;
+}
+
+template <typename S>
+__global__ void k_fields(const S* __restrict__ s, P2<typename Store<S>::R> p, double gbeta,
+                         double T0, double* rho, double* T, double* u, double* v) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const NodeState n = node_state(s, (size_t)y * p.pitch + x, p.plane, gbeta, T0);
+  const size_t node = (size_t)y * p.nx + x;
+  if (rho) rho[node] = n.rho;
+  if (T) T[node] = n.T;
+  if (u) u[node] = n.ux;
+  if (v) v[node] = n.uy;
+}
+
+template <typename S>
+__global__ void k_pops(const S* __restrict__ s, P2<typename Store<S>::R> p, double* f,
+                       double* g) {
+  using R = typename Store<S>::R;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const size_t nodes = (size_t)p.nx * p.ny, node = (size_t)y * p.nx + x;
+  const size_t idx = (size_t)y * p.pitch + x;
+  const double t0 = (1.0 - (double)p.a_T) * 0.2, ti = (4.0 + (double)p.a_T) * 0.05;
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    f[i * nodes + node] = (double)Store<S>::ld(s + i * p.plane + idx) + wrest<double>(i);
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+    g[i * nodes + node] =
+        (double)Store<S>::ld(s + (9 + i) * p.plane + idx) + (i == 0 ? t0 : ti) * (double)p.T0;
+}
+
+// FP64 reductions of the current state (Sec. 3): every node adds its
+// midpoint-rule weighted contributions; nodes in the planes next to the
+// isothermal walls and on the centre line add the temperature sums from
+// which the host finishes Eq. (17) and Nu_middle.
+template <typename S>
+__global__ void __launch_bounds__(256)
+    k_reduce(const S* __restrict__ s, P2<typename Store<S>::R> p, double gbeta, double T0,
+             const double* __restrict__ Wx, const double* __restrict__ Wy, double* partial) {
+  double acc[RED_COUNT];
+#pragma unroll
+  for (int k = 0; k < RED_COUNT; ++k) acc[k] = 0.0;
+  const long long nodes = (long long)p.nx * p.ny;
+  const int mL = (p.nx % 2 == 0) ? p.nx / 2 - 1 : (p.nx - 1) / 2 - 1;  // left column of the centre pair
+  const int mR = (p.nx % 2 == 0) ? p.nx / 2 : (p.nx + 1) / 2;           // right column
+  const int mC = (p.nx % 2 == 0) ? -1 : (p.nx - 1) / 2;                  // centre column (odd n)
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nodes;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(k / p.nx), x = (int)(k - (long long)y * p.nx);
+    const NodeState n = node_state(s, (size_t)y * p.pitch + x, p.plane, gbeta, T0);
+    const double W = Wx[x] * Wy[y];
+    const double u2 = n.ux * n.ux + n.uy * n.uy;
+    const double sp = sqrt(u2);
+    const double Tr = n.T - T0;
+    acc[RED_MASS] += W * n.rho;
+    acc[RED_UT] += W * n.ux * Tr;
+    acc[RED_SPEED] += W * sp;
+    acc[RED_SPEED_UV] += W * sp;
+    acc[RED_U2] += W * u2;
+    const double wy = Wy[y];
+    if (x == 0) acc[RED_HOT1] += wy * n.T;
+    if (x == 1) acc[RED_HOT2] += wy * n.T;
+    if (x == p.nx - 1) acc[RED_COLD1] += wy * n.T;
+    if (x == p.nx - 2) acc[RED_COLD2] += wy * n.T;
+    if (x == mL) acc[RED_MIDTL] += wy * n.T;
+    if (x == mR) acc[RED_MIDTR] += wy * n.T;
+    if (mC < 0 && (x == mL || x == mR)) acc[RED_MIDCONV] += 0.5 * wy * n.ux * Tr;
+    if (x == mC) acc[RED_MIDCONV] += wy * n.ux * Tr;
+    const bool finite = isfinite(n.rho) && isfinite(n.ux) && isfinite(n.uy) && isfinite(n.T);
+    if (!finite) acc[RED_NONFINITE] += 1.0;
+    acc[RED_MAXSPEED] = fmax(acc[RED_MAXSPEED], finite ? sp : 0.0);
+  }
+  __shared__ double sh[8][RED_COUNT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < RED_COUNT; ++k) {
+    const double v = (k == RED_MAXSPEED) ? warp_max(acc[k]) : warp_sum(acc[k]);
+    if (lane == 0) sh[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < RED_COUNT) {
+    const int k = threadIdx.x;
+    double v = sh[0][k];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      v = (k == RED_MAXSPEED) ? fmax(v, sh[w][k]) : v + sh[w][k];
+    partial[(size_t)blockIdx.x * RED_STRIDE + k] = v;
+  }
+}
+
+// One warp per slot sums the block partials in a fixed order (deterministic).
+__global__ void k_finish(const double* __restrict__ partial, int blocks, double* out) {
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (k >= RED_COUNT) return;
+  double v = 0.0;
+  for (int b = lane; b < blocks; b += 32) {
+    const double x = partial[(size_t)b * RED_STRIDE + k];
+    v = (k == RED_MAXSPEED) ? fmax(v, x) : v + x;
+  }
+  v = (k == RED_MAXSPEED) ? warp_max(v) : warp_sum(v);
+  if (lane == 0) out[k] = v;
+}
+
+template <typename R>
+P2<R> make_params(const Solver& s) {
+  P2<R> p;
+  p.nx = s.n[0];
+  p.ny = s.n[1];
+  p.pitch = s.pitch;
+  p.plane = s.plane;
+  for (int k = 0; k < 2; ++k) {
+    p.bx[k] = s.dax[0].base[k];
+    p.wx[k] = static_cast<const R*>(s.dax[0].w[k]);
+    p.by[k] = s.dax[1].base[k];
+    p.wy[k] = static_cast<const R*>(s.dax[1].w[k]);
+  }
+  const Physics& h = s.ph;
+  p.gbeta = R(h.gbeta);
+  p.T0 = R(h.T0);
+  p.s_e = R(h.s_e);
+  p.s_eps = R(h.s_eps);
+  p.s_q = R(h.s_q);
+  p.s_nu = R(h.s_nu);
+  p.q_j = R(h.q_j);
+  p.q_e = R(h.q_e);
+  p.q_nu = R(h.q_nu);
+  p.a_T = R(h.a_T);
+  p.abb_hot = R(h.omega * (h.T_hot - h.T0));
+  p.abb_cold = R(h.omega * (h.T_cold - h.T0));
+  return p;
+}
+
+dim3 block2() { return dim3(32, 8); }
+dim3 grid2(const Solver& s) { return dim3((s.n[0] + 31) / 32, (s.n[1] + 7) / 8); }
+
+// Dispatch on the storage type.
+template <template <typename> class Fn, typename... A>
+cudaError_t dispatch(Solver& s, A... a) {
+  switch (s.precision) {
+    case ISLBM_FP64: return Fn<double>::run(s, a...);
+    case ISLBM_FP32: return Fn<float>::run(s, a...);
+    case ISLBM_FP16DEV: return Fn<__half>::run(s, a...);
+    case ISLBM_BF16DEV: return Fn<__nv_bfloat16>::run(s, a...);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename S>
+struct StepFn {
+  static cudaError_t run(Solver& s) {
+    using R = typename Store<S>::R;
+    const P2<R> p = make_params<R>(s);
+    const S* in = static_cast<const S*>(s.buf[s.cur]);
+    S* out = static_cast<S*>(s.buf[s.cur ^ 1]);
+    if (s.uniform)
+      k_step<S, true><<<grid2(s), block2(), 0, s.stream>>>(in, out, p);
+    else
+      k_step<S, false><<<grid2(s), block2(), 0, s.stream>>>(in, out, p);
+    return cudaGetLastError();
+  }
+};
+
+template <typename S>
+struct InitFieldsFn {
+  static cudaError_t run(Solver& s, const double* rho, const double* T, const double* u,
+                         const double* v) {
+    using R = typename Store<S>::R;
+    k_init_fields<S><<<grid2(s), block2(), 0, s.stream>>>(static_cast<S*>(s.buf[s.cur]),
+                                                         make_params<R>(s), rho, T, u, v);
+    return cudaGetLastError();
+  }
+};
+
+template <typename S>
+struct InitPopsFn {
+  static cudaError_t run(Solver& s, const double* f, const double* g) {
+    using R = typename Store<S>::R;
+    k_init_pops<S><<<grid2(s), block2(), 0, s.stream>>>(static_cast<S*>(s.buf[s.cur]),
+                                                       make_params<R>(s), f, g);
+    return cudaGetLastError();
+  }
+};
+
+template <typename S>
+struct FieldsFn {
+  static cudaError_t run(Solver& s, double* rho, double* T, double* u, double* v) {
+    using R = typename Store<S>::R;
+    k_fields<S><<<grid2(s), block2(), 0, s.stream>>>(static_cast<const S*>(s.buf[s.cur]),
+                                                    make_params<R>(s), s.ph.gbeta, s.ph.T0, rho,
+                                                    T, u, v);
+    return cudaGetLastError();
+  }
+};
+
+template <typename S>
+struct PopsFn {
+  static cudaError_t run(Solver& s, double* f, double* g) {
+    using R = typename Store<S>::R;
+    k_pops<S><<<grid2(s), block2(), 0, s.stream>>>(static_cast<const S*>(s.buf[s.cur]),
+                                                  make_params<R>(s), f, g);
+    return cudaGetLastError();
+  }
+};
+
+template <typename S>
+struct ReduceFn {
+  static cudaError_t run(Solver& s) {
+    using R = typename Store<S>::R;
+    k_reduce<S><<<s.red_blocks, 256, 0, s.stream>>>(
+        static_cast<const S*>(s.buf[s.cur]), make_params<R>(s), s.ph.gbeta, s.ph.T0,
+        s.dax[0].W, s.dax[1].W, s.dscratch);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace
+
+cudaError_t launch_step(Solver& s) {
+  if (s.dim == 3) return launch_step_3d(s);
+  cudaError_t e = dispatch<StepFn>(s);
+  if (e == cudaSuccess) s.cur ^= 1;
+  return e;
+}
+
+cudaError_t launch_init_fields(Solver& s, const double* rho, const double* T, const double* u0,
+                               const double* u1, const double* u2) {
+  if (s.dim == 3) return launch_init_fields_3d(s, rho, T, u0, u1, u2);
+  return dispatch<InitFieldsFn>(s, rho, T, u0, u1);
+}
+
+cudaError_t launch_init_populations(Solver& s, const double* f, const double* g) {
+  if (s.dim == 3) return launch_init_populations_3d(s, f, g);
+  return dispatch<InitPopsFn>(s, f, g);
+}
+
+cudaError_t launch_fields(Solver& s, double* rho, double* T, double* u0, double* u1,
+                          double* u2) {
+  if (s.dim == 3) return launch_fields_3d(s, rho, T, u0, u1, u2);
+  return dispatch<FieldsFn>(s, rho, T, u0, u1);
+}
+
+cudaError_t launch_populations(Solver& s, double* f, double* g) {
+  if (s.dim == 3) return launch_populations_3d(s, f, g);
+  return dispatch<PopsFn>(s, f, g);
+}
+
+cudaError_t launch_reduce(Solver& s) {
+  cudaError_t e = (s.dim == 3) ? launch_reduce_3d(s) : dispatch<ReduceFn>(s);
+  if (e != cudaSuccess) return e;
+  return launch_finish_reduce(s);
+}
+
+cudaError_t launch_finish_reduce(Solver& s) {
+  k_finish<<<1, 32 * RED_COUNT, 0, s.stream>>>(s.dscratch, s.red_blocks, s.dresult);
+  return cudaGetLastError();
+}
+
+}  // namespace islbm

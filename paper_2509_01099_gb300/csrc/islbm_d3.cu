@@ -1,0 +1,599 @@
+// 3-D kernels: D3Q19 flow + D3Q7 temperature populations (Sec. 2.1 - 2.3, Sec. 4).
+//
+// Storage: one plane per population, [q][z][y][x] with a padded x pitch;
+// planes 0..18 hold the flow populations, 19..25 the temperature populations,
+// in the velocity order
+//   D3Q19: 0 | +x -x +y -y +z -z | (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0)
+//          (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+//   D3Q7:  0 | +x -x +y -y +z -z
+// As in 2-D, the stored state is the post-collision deviation, and one step is
+// pull (interpolated virtual streaming or wall rule) -> macroscopic moments ->
+// MRT collision -> store.  Hot wall at x = 0, cold wall at x = 1, the y and z
+// walls adiabatic; gravity along -y.
+#include "islbm_internal.h"
+#include "islbm_store.cuh"
+
+namespace islbm {
+namespace {
+
+template <typename R>
+struct P3 {
+  int nx, ny, nz, pitch;
+  long long plane;
+  const int* b[3][2];
+  const R* w[3][2];
+  R gbeta, T0, s_e, s_eps, s_q, s_nu, s_pi, s_m, q_j, q_e, q_nu, a_T;
+  R abb_hot, abb_cold;
+};
+
+template <typename R>
+__device__ __forceinline__ R wrest3(int i) {
+  return i == 0 ? R(1.0 / 3.0) : (i < 7 ? R(1.0 / 18.0) : R(1.0 / 36.0));
+}
+
+// MRT collision of one node in deviation form (Sec. 2.1), d'Humieres moment basis
+// (rho, e, eps, jx, qx, jy, qy, jz, qz, 3pxx, 3pixx, pww, piww, pxy, pyz, pxz,
+// mx, my, mz) with the printed m_eq and M F~; f+ = f + M^T diag(1/|row|^2) dm.
+// Temperature: D3Q7 rows (T, jx, jy, jz, -6+7|c|^2, 3cx^2-|c|^2, cy^2-cz^2).
+template <typename R>
+__device__ __forceinline__ void collide3(R (&f)[19], R (&g)[7], const P3<R>& p, R& rho_o,
+                                         R& ux_o, R& uy_o, R& uz_o, R& T_o) {
+  const R sax = ((f[1] + f[2]) + (f[3] + f[4])) + (f[5] + f[6]);
+  const R exy = (f[7] + f[8]) + (f[9] + f[10]);
+  const R exz = (f[11] + f[12]) + (f[13] + f[14]);
+  const R eyz = (f[15] + f[16]) + (f[17] + f[18]);
+  const R sed = exy + exz + eyz;
+  const R drho = f[0] + sax + sed;
+  const R rho = R(1) + drho;
+  // odd combinations of the edge populations
+  const R xy_x = (f[7] - f[8]) + (f[9] - f[10]);    // sum cx over xy edges
+  const R xy_y = (f[7] - f[8]) - (f[9] - f[10]);    // sum cy over xy edges
+  const R xz_x = (f[11] - f[12]) + (f[13] - f[14]);
+  const R xz_z = (f[11] - f[12]) - (f[13] - f[14]);
+  const R yz_y = (f[15] - f[16]) + (f[17] - f[18]);
+  const R yz_z = (f[15] - f[16]) - (f[17] - f[18]);
+  const R jx = (f[1] - f[2]) + xy_x + xz_x;
+  const R jy = (f[3] - f[4]) + xy_y + yz_y;
+  const R jz = (f[5] - f[6]) + xz_z + yz_z;
+  const R Tr = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
+  const R T = Tr + p.T0;
+  const R Fy = rho * p.gbeta * Tr;
+  const R inv = R(1) / rho;
+  const R ux = jx * inv, uy = (jy + R(0.5) * Fy) * inv, uz = jz * inv;
+  const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+  const R rusq = rho * (ux2 + uy2 + uz2);
+  const R uF = uy * Fy;
+
+  const R m1 = R(-30) * f[0] - R(11) * sax + R(8) * sed;
+  const R m2 = R(12) * f[0] - R(4) * sax + sed;
+  const R m4 = R(-4) * (f[1] - f[2]) + xy_x + xz_x;
+  const R m6 = R(-4) * (f[3] - f[4]) + xy_y + yz_y;
+  const R m8 = R(-4) * (f[5] - f[6]) + xz_z + yz_z;
+  const R axx = f[1] + f[2], ayy = f[3] + f[4], azz = f[5] + f[6];
+  const R m9 = R(2) * axx - (ayy + azz) + (exy + exz) - R(2) * eyz;
+  const R m10 = R(-4) * axx + R(2) * (ayy + azz) + (exy + exz) - R(2) * eyz;
+  const R m11 = (ayy - azz) + (exy - exz);
+  const R m12 = R(-2) * (ayy - azz) + (exy - exz);
+  const R m13 = (f[7] + f[8]) - (f[9] + f[10]);
+  const R m14 = (f[15] + f[16]) - (f[17] + f[18]);
+  const R m15 = (f[11] + f[12]) - (f[13] + f[14]);
+  const R m16 = xy_x - xz_x;
+  const R m17 = yz_y - xy_y;
+  const R m18 = xz_z - yz_z;
+
+  const R pxx = R(2) * ux2 - uy2 - uz2, pww = uy2 - uz2;
+  const R dm1 = -p.s_e * (m1 + R(11) * drho - R(19) * rusq) + (R(1) - R(0.5) * p.s_e) * R(38) * uF;
+  const R dm2 = -p.s_eps * (m2 - R(3) * drho + R(5.5) * rusq) - (R(1) - R(0.5) * p.s_eps) * R(11) * uF;
+  const R dm4 = -p.s_q * (m4 + R(2.0 / 3.0) * rho * ux);
+  const R dm5 = Fy;
+  const R dm6 = -p.s_q * (m6 + R(2.0 / 3.0) * rho * uy) - (R(1) - R(0.5) * p.s_q) * R(2.0 / 3.0) * Fy;
+  const R dm8 = -p.s_q * (m8 + R(2.0 / 3.0) * rho * uz);
+  const R dm9 = -p.s_nu * (m9 - rho * pxx) - (R(1) - R(0.5) * p.s_nu) * R(2) * uF;
+  const R dm10 = -p.s_pi * (m10 + R(0.5) * rho * pxx) + (R(1) - R(0.5) * p.s_pi) * uF;
+  const R dm11 = -p.s_nu * (m11 - rho * pww) + (R(1) - R(0.5) * p.s_nu) * R(2) * uF;
+  const R dm12 = -p.s_pi * (m12 + R(0.5) * rho * pww) - (R(1) - R(0.5) * p.s_pi) * uF;
+  const R dm13 = -p.s_nu * (m13 - rho * ux * uy) + (R(1) - R(0.5) * p.s_nu) * ux * Fy;
+  const R dm14 = -p.s_nu * (m14 - rho * uy * uz) + (R(1) - R(0.5) * p.s_nu) * uz * Fy;
+  const R dm15 = -p.s_nu * (m15 - rho * ux * uz);
+  const R dm16 = -p.s_m * m16, dm17 = -p.s_m * m17, dm18 = -p.s_m * m18;
+
+  const R a1 = dm1 * R(1.0 / 2394.0), a2 = dm2 * R(1.0 / 252.0);
+  const R a4 = dm4 * R(1.0 / 40.0), a5 = dm5 * R(0.1), a6 = dm6 * R(1.0 / 40.0);
+  const R a8 = dm8 * R(1.0 / 40.0);
+  const R a9 = dm9 * R(1.0 / 36.0), a10 = dm10 * R(1.0 / 72.0);
+  const R a11 = dm11 * R(1.0 / 12.0), a12 = dm12 * R(1.0 / 24.0);
+  const R a13 = dm13 * R(0.25), a14 = dm14 * R(0.25), a15 = dm15 * R(0.25);
+  const R a16 = dm16 * R(0.125), a17 = dm17 * R(0.125), a18 = dm18 * R(0.125);
+
+  const R cax = R(-11) * a1 - R(4) * a2;
+  const R ced = R(8) * a1 + a2;
+  f[0] += R(-30) * a1 + R(12) * a2;
+  const R xx = R(2) * a9 - R(4) * a10;                 // x-axis pair, even part
+  const R yy = -a9 + R(2) * a10 + a11 - R(2) * a12;    // y-axis pair
+  const R zz = -a9 + R(2) * a10 - a11 + R(2) * a12;    // z-axis pair
+  f[1] += cax + xx - R(4) * a4;
+  f[2] += cax + xx + R(4) * a4;
+  f[3] += cax + yy + a5 - R(4) * a6;
+  f[4] += cax + yy - a5 + R(4) * a6;
+  f[5] += cax + zz - R(4) * a8;
+  f[6] += cax + zz + R(4) * a8;
+  const R exy_e = ced + a9 + a10 + a11 + a12;          // even part of the xy edges
+  const R exz_e = ced + a9 + a10 - a11 - a12;
+  const R eyz_e = ced - R(2) * a9 - R(2) * a10;
+  const R px = a4, py = a5 + a6, pz = a8;                // odd parts (jx = jz = 0 increments)
+  f[7] += exy_e + px + py + a13 + a16 - a17;
+  f[8] += exy_e - px - py + a13 - a16 + a17;
+  f[9] += exy_e + px - py - a13 + a16 + a17;
+  f[10] += exy_e - px + py - a13 - a16 - a17;
+  f[11] += exz_e + px + pz + a15 - a16 + a18;
+  f[12] += exz_e - px - pz + a15 + a16 - a18;
+  f[13] += exz_e + px - pz - a15 - a16 - a18;
+  f[14] += exz_e - px + pz - a15 + a16 + a18;
+  f[15] += eyz_e + py + pz + a14 + a17 - a18;
+  f[16] += eyz_e - py - pz + a14 - a17 + a18;
+  f[17] += eyz_e + py - pz - a14 + a17 + a18;
+  f[18] += eyz_e - py + pz - a14 - a17 - a18;
+
+  const R n1 = g[1] - g[2], n2 = g[3] - g[4], n3 = g[5] - g[6];
+  const R n4 = R(-6) * g[0] + ((g[1] + g[2]) + (g[3] + g[4])) + (g[5] + g[6]);
+  const R n5 = R(2) * (g[1] + g[2]) - ((g[3] + g[4]) + (g[5] + g[6]));
+  const R n6 = (g[3] + g[4]) - (g[5] + g[6]);
+  const R b1 = R(-0.5) * p.q_j * (n1 - ux * T);
+  const R b2 = R(-0.5) * p.q_j * (n2 - uy * T);
+  const R b3 = R(-0.5) * p.q_j * (n3 - uz * T);
+  const R b4 = -p.q_e * (n4 - p.a_T * Tr) * R(1.0 / 42.0);
+  const R b5 = -p.q_nu * n5 * R(1.0 / 12.0);
+  const R b6 = R(-0.25) * p.q_nu * n6;
+  g[0] += R(-6) * b4;
+  g[1] += b1 + b4 + R(2) * b5;
+  g[2] += -b1 + b4 + R(2) * b5;
+  g[3] += b2 + b4 - b5 + b6;
+  g[4] += -b2 + b4 - b5 + b6;
+  g[5] += b3 + b4 - b5 - b6;
+  g[6] += -b3 + b4 - b5 - b6;
+  rho_o = rho;
+  ux_o = ux;
+  uy_o = uy;
+  uz_o = uz;
+  T_o = T;
+}
+
+// Separable quadratic interpolation of one population at node (x, y, z)
+// (Sec. 2.2).  At most two axes move for D3Q19.
+template <typename S, typename R, int CX, int CY, int CZ, bool UNI>
+__device__ __forceinline__ R pull3(const S* __restrict__ pl, int x, int y, int z,
+                                   const P3<R>& p) {
+  using St = Store<S>;
+  const size_t sy = p.pitch, sz = (size_t)p.pitch * p.ny;
+  if (UNI || (CX == 0 && CY == 0 && CZ == 0))
+    return St::ld(pl + (size_t)(z - CZ) * sz + (size_t)(y - CY) * sy + (x - CX));
+  // the (up to) two moving axes
+  int base0 = 0, base1 = 0;
+  const R* w0 = nullptr;
+  const R* w1 = nullptr;
+  size_t st0 = 0, st1 = 0;
+  size_t origin = (size_t)z * sz + (size_t)y * sy + x;
+  int na = 0;
+  if (CX != 0) {
+    constexpr int k = CX > 0 ? 0 : 1;
+    base0 = __ldg(p.b[0][k] + x);
+    w0 = p.w[0][k] + 3 * x;
+    st0 = 1;
+    origin -= x;
+    na = 1;
+  }
+  if (CY != 0) {
+    constexpr int k = CY > 0 ? 0 : 1;
+    const int b = __ldg(p.b[1][k] + y);
+    const R* w = p.w[1][k] + 3 * y;
+    origin -= (size_t)y * sy;
+    if (na == 0) { base0 = b; w0 = w; st0 = sy; na = 1; }
+    else { base1 = b; w1 = w; st1 = sy; na = 2; }
+  }
+  if (CZ != 0) {
+    constexpr int k = CZ > 0 ? 0 : 1;
+    const int b = __ldg(p.b[2][k] + z);
+    const R* w = p.w[2][k] + 3 * z;
+    origin -= (size_t)z * sz;
+    if (na == 0) { base0 = b; w0 = w; st0 = sz; na = 1; }
+    else { base1 = b; w1 = w; st1 = sz; na = 2; }
+  }
+  const S* o = pl + origin + (size_t)base0 * st0;
+  const R a0 = __ldg(w0), a1 = __ldg(w0 + 1), a2 = __ldg(w0 + 2);
+  if (na == 1) return a0 * St::ld(o) + a1 * St::ld(o + st0) + a2 * St::ld(o + 2 * st0);
+  o += (size_t)base1 * st1;
+  R acc = R(0);
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const S* r = o + l * st1;
+    acc += __ldg(w1 + l) * (a0 * St::ld(r) + a1 * St::ld(r + st0) + a2 * St::ld(r + 2 * st0));
+  }
+  return acc;
+}
+
+template <typename S, bool UNI>
+__global__ void __launch_bounds__(256)
+    k_step3(const S* __restrict__ fin, S* __restrict__ fout, P3<typename Store<S>::R> p) {
+  using R = typename Store<S>::R;
+  using St = Store<S>;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= p.nx || y >= p.ny) return;
+  const size_t idx = ((size_t)z * p.ny + y) * p.pitch + x;
+  const long long P = p.plane;
+  const bool wxm = x == 0, wxp = x == p.nx - 1, wym = y == 0, wyp = y == p.ny - 1;
+  const bool wzm = z == 0, wzp = z == p.nz - 1;
+  R f[19], g[7];
+#define BB(i, o) St::ld(fin + (o) * P + idx)
+#define PL(i, cx, cy, cz) pull3<S, R, cx, cy, cz, UNI>(fin + (i) * P, x, y, z, p)
+  f[0] = St::ld(fin + idx);
+  f[1] = wxm ? BB(1, 2) : PL(1, 1, 0, 0);
+  f[2] = wxp ? BB(2, 1) : PL(2, -1, 0, 0);
+  f[3] = wym ? BB(3, 4) : PL(3, 0, 1, 0);
+  f[4] = wyp ? BB(4, 3) : PL(4, 0, -1, 0);
+  f[5] = wzm ? BB(5, 6) : PL(5, 0, 0, 1);
+  f[6] = wzp ? BB(6, 5) : PL(6, 0, 0, -1);
+  f[7] = (wxm || wym) ? BB(7, 8) : PL(7, 1, 1, 0);
+  f[8] = (wxp || wyp) ? BB(8, 7) : PL(8, -1, -1, 0);
+  f[9] = (wxm || wyp) ? BB(9, 10) : PL(9, 1, -1, 0);
+  f[10] = (wxp || wym) ? BB(10, 9) : PL(10, -1, 1, 0);
+  f[11] = (wxm || wzm) ? BB(11, 12) : PL(11, 1, 0, 1);
+  f[12] = (wxp || wzp) ? BB(12, 11) : PL(12, -1, 0, -1);
+  f[13] = (wxm || wzp) ? BB(13, 14) : PL(13, 1, 0, -1);
+  f[14] = (wxp || wzm) ? BB(14, 13) : PL(14, -1, 0, 1);
+  f[15] = (wym || wzm) ? BB(15, 16) : PL(15, 0, 1, 1);
+  f[16] = (wyp || wzp) ? BB(16, 15) : PL(16, 0, -1, -1);
+  f[17] = (wym || wzp) ? BB(17, 18) : PL(17, 0, 1, -1);
+  f[18] = (wyp || wzm) ? BB(18, 17) : PL(18, 0, -1, 1);
+  g[0] = St::ld(fin + 19 * P + idx);
+  g[1] = wxm ? p.abb_hot - BB(20, 21) : PL(20, 1, 0, 0);
+  g[2] = wxp ? p.abb_cold - BB(21, 20) : PL(21, -1, 0, 0);
+  g[3] = wym ? BB(22, 23) : PL(22, 0, 1, 0);
+  g[4] = wyp ? BB(23, 22) : PL(23, 0, -1, 0);
+  g[5] = wzm ? BB(24, 25) : PL(24, 0, 0, 1);
+  g[6] = wzp ? BB(25, 24) : PL(25, 0, 0, -1);
+#undef BB
+#undef PL
+  R rho, ux, uy, uz, T;
+  collide3(f, g, p, rho, ux, uy, uz, T);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) St::st(fout + i * P + idx, f[i]);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) St::st(fout + (19 + i) * P + idx, g[i]);
+}
+
+__device__ __constant__ int kE3[19][3] = {
+    {0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+    {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1}, {-1, 0, -1}, {1, 0, -1},
+    {-1, 0, 1}, {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+// Equilibrium (Sec. 2.1) of given fields, then the collision: the second-order
+// Hermite flow equilibrium (whose moments are the printed m_eq) and
+// g_0 = t_0 T, g_i = t_i T + (e_i.u) T / 2 with t_0 = (1-a_T)/7, t_i = (6+a_T)/42.
+template <typename S>
+__global__ void k_init_fields3(S* __restrict__ fout, P3<typename Store<S>::R> p,
+                               const double* __restrict__ rho_in, const double* __restrict__ T_in,
+                               const double* __restrict__ u_in, const double* __restrict__ v_in,
+                               const double* __restrict__ w_in) {
+  using R = typename Store<S>::R;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= p.nx || y >= p.ny) return;
+  const size_t node = ((size_t)z * p.ny + y) * p.nx + x;
+  const R rho = rho_in ? R(rho_in[node]) : R(1);
+  const R T = R(T_in[node]);
+  const R ux = u_in ? R(u_in[node]) : R(0);
+  const R uy = v_in ? R(v_in[node]) : R(0);
+  const R uz = w_in ? R(w_in[node]) : R(0);
+  const R usq = ux * ux + uy * uy + uz * uz;
+  R f[19], g[7];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const R eu = R(kE3[i][0]) * ux + R(kE3[i][1]) * uy + R(kE3[i][2]) * uz;
+    f[i] = wrest3<R>(i) * (rho * (R(1) + R(3) * eu + R(4.5) * eu * eu - R(1.5) * usq) - R(1));
+  }
+  const R t0 = (R(1) - p.a_T) / R(7), ti = (R(6) + p.a_T) / R(42);
+  const R Tr = T - p.T0;
+  g[0] = t0 * Tr;
+#pragma unroll
+  for (int i = 1; i < 7; ++i)
+    g[i] = ti * Tr + R(0.5) * (R(kE3[i][0]) * ux + R(kE3[i][1]) * uy + R(kE3[i][2]) * uz) * T;
+  R r_, a_, b_, c_, d_;
+  collide3(f, g, p, r_, a_, b_, c_, d_);
+  const size_t idx = ((size_t)z * p.ny + y) * p.pitch + x;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) Store<S>::st(fout + i * p.plane + idx, f[i]);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) Store<S>::st(fout + (19 + i) * p.plane + idx, g[i]);
+}
+
+template <typename S>
+__global__ void k_init_pops3(S* __restrict__ fout, P3<typename Store<S>::R> p,
+                             const double* __restrict__ fin, const double* __restrict__ gin) {
+  using R = typename Store<S>::R;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= p.nx || y >= p.ny) return;
+  const size_t nodes = (size_t)p.nx * p.ny * p.nz;
+  const size_t node = ((size_t)z * p.ny + y) * p.nx + x;
+  const R t0 = (R(1) - p.a_T) / R(7), ti = (R(6) + p.a_T) / R(42);
+  R f[19], g[7];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) f[i] = R(fin[i * nodes + node] - wrest3<double>(i));
+#pragma unroll
+  for (int i = 0; i < 7; ++i) g[i] = R(gin[i * nodes + node]) - (i == 0 ? t0 : ti) * p.T0;
+  R r_, a_, b_, c_, d_;
+  collide3(f, g, p, r_, a_, b_, c_, d_);
+  const size_t idx = ((size_t)z * p.ny + y) * p.pitch + x;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) Store<S>::st(fout + i * p.plane + idx, f[i]);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) Store<S>::st(fout + (19 + i) * p.plane + idx, g[i]);
+}
+
+struct NodeState3 {
+  double rho, ux, uy, uz, T;
+};
+
+template <typename S>
+__device__ __forceinline__ NodeState3 node_state3(const S* __restrict__ s, size_t idx,
+                                                  long long P, double gbeta, double T0) {
+  double f[19], g[7];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) f[i] = (double)Store<S>::ld(s + i * P + idx);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) g[i] = (double)Store<S>::ld(s + (19 + i) * P + idx);
+  double drho = 0, jx = 0, jy = 0, jz = 0, Tr = 0;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    drho += f[i];
+    jx += kE3[i][0] * f[i];
+    jy += kE3[i][1] * f[i];
+    jz += kE3[i][2] * f[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 7; ++i) Tr += g[i];
+  NodeState3 n;
+  n.rho = 1.0 + drho;
+  n.T = Tr + T0;
+  const double Fy = n.rho * gbeta * Tr;
+  n.ux = jx / n.rho;
+  n.uy = (jy - 0.5 * Fy) / n.rho;
+  n.uz = jz / n.rho;
+  return n;
+}
+
+template <typename S>
+__global__ void k_fields3(const S* __restrict__ s, P3<typename Store<S>::R> p, double gbeta,
+                          double T0, double* rho, double* T, double* u, double* v, double* w) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= p.nx || y >= p.ny) return;
+  const NodeState3 n = node_state3(s, ((size_t)z * p.ny + y) * p.pitch + x, p.plane, gbeta, T0);
+  const size_t node = ((size_t)z * p.ny + y) * p.nx + x;
+  if (rho) rho[node] = n.rho;
+  if (T) T[node] = n.T;
+  if (u) u[node] = n.ux;
+  if (v) v[node] = n.uy;
+  if (w) w[node] = n.uz;
+}
+
+template <typename S>
+__global__ void k_pops3(const S* __restrict__ s, P3<typename Store<S>::R> p, double* f,
+                        double* g) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= p.nx || y >= p.ny) return;
+  const size_t nodes = (size_t)p.nx * p.ny * p.nz;
+  const size_t node = ((size_t)z * p.ny + y) * p.nx + x;
+  const size_t idx = ((size_t)z * p.ny + y) * p.pitch + x;
+  const double t0 = (1.0 - (double)p.a_T) / 7.0, ti = (6.0 + (double)p.a_T) / 42.0;
+#pragma unroll
+  for (int i = 0; i < 19; ++i)
+    f[i * nodes + node] = (double)Store<S>::ld(s + i * p.plane + idx) + wrest3<double>(i);
+#pragma unroll
+  for (int i = 0; i < 7; ++i)
+    g[i * nodes + node] =
+        (double)Store<S>::ld(s + (19 + i) * p.plane + idx) + (i == 0 ? t0 : ti) * (double)p.T0;
+}
+
+// FP64 reductions (Sec. 4): volume sums and the wall-plane temperature sums of
+// Eq. (17) with the wall-plane weights W_y W_z.
+template <typename S>
+__global__ void __launch_bounds__(256)
+    k_reduce3(const S* __restrict__ s, P3<typename Store<S>::R> p, double gbeta, double T0,
+              const double* __restrict__ Wx, const double* __restrict__ Wy,
+              const double* __restrict__ Wz, double* partial) {
+  double acc[RED_COUNT];
+#pragma unroll
+  for (int k = 0; k < RED_COUNT; ++k) acc[k] = 0.0;
+  const long long nodes = (long long)p.nx * p.ny * p.nz;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nodes;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(k % p.nx);
+    const long long r = k / p.nx;
+    const int y = (int)(r % p.ny), z = (int)(r / p.ny);
+    const NodeState3 n = node_state3(s, ((size_t)z * p.ny + y) * p.pitch + x, p.plane, gbeta, T0);
+    const double wp = Wy[y] * Wz[z];
+    const double W = Wx[x] * wp;
+    const double u2 = n.ux * n.ux + n.uy * n.uy + n.uz * n.uz;
+    const double sp = sqrt(u2);
+    const double Tr = n.T - T0;
+    acc[RED_MASS] += W * n.rho;
+    acc[RED_UT] += W * n.ux * Tr;
+    acc[RED_SPEED] += W * sp;
+    acc[RED_SPEED_UV] += W * sqrt(n.ux * n.ux + n.uy * n.uy);
+    acc[RED_U2] += W * u2;
+    if (x == 0) acc[RED_HOT1] += wp * n.T;
+    if (x == 1) acc[RED_HOT2] += wp * n.T;
+    if (x == p.nx - 1) acc[RED_COLD1] += wp * n.T;
+    if (x == p.nx - 2) acc[RED_COLD2] += wp * n.T;
+    const bool finite = isfinite(n.rho) && isfinite(n.ux) && isfinite(n.uy) && isfinite(n.uz) &&
+                        isfinite(n.T);
+    if (!finite) acc[RED_NONFINITE] += 1.0;
+    acc[RED_MAXSPEED] = fmax(acc[RED_MAXSPEED], finite ? sp : 0.0);
+  }
+  __shared__ double sh[8][RED_COUNT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < RED_COUNT; ++k) {
+    const double v = (k == RED_MAXSPEED) ? warp_max(acc[k]) : warp_sum(acc[k]);
+    if (lane == 0) sh[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < RED_COUNT) {
+    const int k = threadIdx.x;
+    double v = sh[0][k];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      v = (k == RED_MAXSPEED) ? fmax(v, sh[w][k]) : v + sh[w][k];
+    partial[(size_t)blockIdx.x * RED_STRIDE + k] = v;
+  }
+}
+
+template <typename R>
+P3<R> make_params3(const Solver& s) {
+  P3<R> p;
+  p.nx = s.n[0];
+  p.ny = s.n[1];
+  p.nz = s.n[2];
+  p.pitch = s.pitch;
+  p.plane = s.plane;
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 2; ++k) {
+      p.b[a][k] = s.dax[a].base[k];
+      p.w[a][k] = static_cast<const R*>(s.dax[a].w[k]);
+    }
+  const Physics& h = s.ph;
+  p.gbeta = R(h.gbeta);
+  p.T0 = R(h.T0);
+  p.s_e = R(h.s_e);
+  p.s_eps = R(h.s_eps);
+  p.s_q = R(h.s_q);
+  p.s_nu = R(h.s_nu);
+  p.s_pi = R(h.s_pi);
+  p.s_m = R(h.s_m);
+  p.q_j = R(h.q_j);
+  p.q_e = R(h.q_e);
+  p.q_nu = R(h.q_nu);
+  p.a_T = R(h.a_T);
+  p.abb_hot = R(h.omega * (h.T_hot - h.T0));
+  p.abb_cold = R(h.omega * (h.T_cold - h.T0));
+  return p;
+}
+
+dim3 block3() { return dim3(32, 8, 1); }
+dim3 grid3(const Solver& s) { return dim3((s.n[0] + 31) / 32, (s.n[1] + 7) / 8, s.n[2]); }
+
+template <template <typename> class Fn, typename... A>
+cudaError_t dispatch3(Solver& s, A... a) {
+  switch (s.precision) {
+    case ISLBM_FP64: return Fn<double>::run(s, a...);
+    case ISLBM_FP32: return Fn<float>::run(s, a...);
+    case ISLBM_FP16DEV: return Fn<__half>::run(s, a...);
+    case ISLBM_BF16DEV: return Fn<__nv_bfloat16>::run(s, a...);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename S>
+struct Step3 {
+  static cudaError_t run(Solver& s) {
+    using R = typename Store<S>::R;
+    const auto p = make_params3<R>(s);
+    const S* in = static_cast<const S*>(s.buf[s.cur]);
+    S* out = static_cast<S*>(s.buf[s.cur ^ 1]);
+    if (s.uniform)
+      k_step3<S, true><<<grid3(s), block3(), 0, s.stream>>>(in, out, p);
+    else
+      k_step3<S, false><<<grid3(s), block3(), 0, s.stream>>>(in, out, p);
+    return cudaGetLastError();
+  }
+};
+
+template <typename S>
+struct InitFields3 {
+  static cudaError_t run(Solver& s, const double* rho, const double* T, const double* u,
+                         const double* v, const double* w) {
+    using R = typename Store<S>::R;
+    k_init_fields3<S><<<grid3(s), block3(), 0, s.stream>>>(static_cast<S*>(s.buf[s.cur]),
+                                                          make_params3<R>(s), rho, T, u, v, w);
+    return cudaGetLastError();
+  }
+};
+
+template <typename S>
+struct InitPops3 {
+  static cudaError_t run(Solver& s, const double* f, const double* g) {
+    using R = typename Store<S>::R;
+    k_init_pops3<S><<<grid3(s), block3(), 0, s.stream>>>(static_cast<S*>(s.buf[s.cur]),
+                                                        make_params3<R>(s), f, g);
+    return cudaGetLastError();
+  }
+};
+
+template <typename S>
+struct Fields3 {
+  static cudaError_t run(Solver& s, double* rho, double* T, double* u, double* v, double* w) {
+    using R = typename Store<S>::R;
+    k_fields3<S><<<grid3(s), block3(), 0, s.stream>>>(static_cast<const S*>(s.buf[s.cur]),
+                                                     make_params3<R>(s), s.ph.gbeta, s.ph.T0,
+                                                     rho, T, u, v, w);
+    return cudaGetLastError();
+  }
+};
+
+template <typename S>
+struct Pops3 {
+  static cudaError_t run(Solver& s, double* f, double* g) {
+    using R = typename Store<S>::R;
+    k_pops3<S><<<grid3(s), block3(), 0, s.stream>>>(static_cast<const S*>(s.buf[s.cur]),
+                                                   make_params3<R>(s), f, g);
+    return cudaGetLastError();
+  }
+};
+
+template <typename S>
+struct Reduce3 {
+  static cudaError_t run(Solver& s) {
+    using R = typename Store<S>::R;
+    k_reduce3<S><<<s.red_blocks, 256, 0, s.stream>>>(
+        static_cast<const S*>(s.buf[s.cur]), make_params3<R>(s), s.ph.gbeta, s.ph.T0,
+        s.dax[0].W, s.dax[1].W, s.dax[2].W, s.dscratch);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace
+
+cudaError_t launch_step_3d(Solver& s) {
+  cudaError_t e = dispatch3<Step3>(s);
+  if (e == cudaSuccess) s.cur ^= 1;
+  return e;
+}
+
+cudaError_t launch_init_fields_3d(Solver& s, const double* rho, const double* T,
+                                  const double* u0, const double* u1, const double* u2) {
+  return dispatch3<InitFields3>(s, rho, T, u0, u1, u2);
+}
+
+cudaError_t launch_init_populations_3d(Solver& s, const double* f, const double* g) {
+  return dispatch3<InitPops3>(s, f, g);
+}
+
+cudaError_t launch_fields_3d(Solver& s, double* rho, double* T, double* u0, double* u1,
+                             double* u2) {
+  return dispatch3<Fields3>(s, rho, T, u0, u1, u2);
+}
+
+cudaError_t launch_populations_3d(Solver& s, double* f, double* g) {
+  return dispatch3<Pops3>(s, f, g);
+}
+
+cudaError_t launch_reduce_3d(Solver& s) { return dispatch3<Reduce3>(s); }
+
+}  // namespace islbm

@@ -1,0 +1,120 @@
+// Internal declarations of the GB300 ISLBM library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/islbm.h"
+
+namespace islbm {
+
+// Reduction accumulator slots (FP64).  The finished vector is copied to the host.
+enum RedSlot {
+  RED_MASS = 0,   // sum rho W
+  RED_UT,         // sum u (T - T0) W
+  RED_SPEED,      // sum |u| W
+  RED_SPEED_UV,   // sum sqrt(u^2 + v^2) W
+  RED_U2,         // sum |u|^2 W
+  RED_HOT1,       // sum T W_perp on the first fluid plane next to the hot wall
+  RED_HOT2,       // ... on the second plane
+  RED_COLD1,      // sum T W_perp on the last fluid plane (cold wall)
+  RED_COLD2,      // ... on the one before it
+  RED_MIDCONV,    // sum u (T - T0) W_y on the centre line (2-D; halved per column for even n)
+  RED_MIDTL,      // sum T W_y on the column left of the centre (2-D)
+  RED_MIDTR,      // sum T W_y on the column right of the centre (2-D)
+  RED_NONFINITE,  // count of non-finite nodes
+  RED_MAXSPEED,   // max |u| (max-reduced)
+  RED_COUNT
+};
+
+constexpr int RED_STRIDE = 16;   // doubles per block partial (>= RED_COUNT)
+
+// Per-axis tables, built once on the host in FP64.
+struct Axis {
+  int n = 0;
+  std::vector<double> X;       // lattice coordinates of ghost + fluid nodes (n + 2)
+  std::vector<double> W;       // midpoint-rule widths of the fluid nodes (n)
+  std::vector<int> base[2];    // [0]: c = +1, [1]: c = -1; first stencil node (0-based), -1 at a wall
+  std::vector<double> w[2];    // 3 Lagrange weights per fluid node
+  bool uniform = false;
+};
+
+// Device view of one axis.  Weights are stored in the compute type.
+struct DevAxis {
+  const int* base[2];
+  const void* w[2];
+  const double* W;
+};
+
+// Lattice-unit physics of a handle.
+struct Physics {
+  double Ra, Pr, Ma, L, u_f, nu, alpha, gbeta, dT;
+  double s_nu, s_e, s_eps, s_q, s_pi, s_m;
+  double q_j, q_e, q_nu, a_T, omega;
+  double T_hot, T_cold, T0;
+  // wall-derivative coefficients (Eq. (17)): dT/dX = cw*T_w + c1*T_1 + c2*T_2
+  double hot_cw, hot_c1, hot_c2, cold_cw, cold_c1, cold_c2;
+  double mid_inv_dx;  // 1/(X_{m+1}-X_m) (even n) or 1/(X_{m+1}-X_{m-1}) (odd n)
+};
+
+struct Solver {
+  int dim = 2, lattice = 0, precision = 1, stencil = 0;
+  int n[3] = {1, 1, 1};
+  int qf = 9, qg = 5;
+  bool uniform = false;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  size_t elem = 4;          // bytes per stored population value
+  int pitch = 0;            // x pitch in elements
+  long long plane = 0;      // elements per population plane
+  long long nodes = 0;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;              // buffer holding the current (post-collision) state
+  long long time = 0;
+  Physics ph{};
+  Axis ax[3];
+  void* dtables = nullptr;
+  DevAxis dax[3]{};
+  double* dscratch = nullptr;     // reduction partials [blocks][RED_COUNT]
+  int red_blocks = 0;
+  double* dresult = nullptr;      // finished reduction vector
+  double* hresult = nullptr;      // pinned host copy
+  double* dfield = nullptr;       // staging for field upload / download (5 * nodes)
+  std::string err;
+  unsigned long long fingerprint = 0;
+};
+
+// ---- kernel launchers (islbm_d2.cu / islbm_d3.cu) ----
+// Equilibrium initialisation followed by a collision; fields are device arrays
+// (rho may be null -> 1; u[2] null in 2-D).  Writes buf[cur].
+cudaError_t launch_init_fields(Solver& s, const double* rho, const double* T, const double* u0,
+                               const double* u1, const double* u2);
+// Collide full FP64 populations (device, [q][node]) and store them into buf[cur].
+cudaError_t launch_init_populations(Solver& s, const double* f, const double* g);
+// One fused step: buf[cur] -> buf[cur ^ 1].
+cudaError_t launch_step(Solver& s);
+// Macroscopic fields of the current state into device arrays (any may be null).
+cudaError_t launch_fields(Solver& s, double* rho, double* T, double* u0, double* u1, double* u2);
+// Full FP64 post-collision populations of the current state, [q][node] device arrays.
+cudaError_t launch_populations(Solver& s, double* f, double* g);
+// Reductions of the current state into s.dresult (RED_COUNT doubles).
+cudaError_t launch_reduce(Solver& s);
+
+cudaError_t launch_init_fields_3d(Solver& s, const double* rho, const double* T,
+                                  const double* u0, const double* u1, const double* u2);
+cudaError_t launch_init_populations_3d(Solver& s, const double* f, const double* g);
+cudaError_t launch_step_3d(Solver& s);
+cudaError_t launch_fields_3d(Solver& s, double* rho, double* T, double* u0, double* u1,
+                             double* u2);
+cudaError_t launch_populations_3d(Solver& s, double* f, double* g);
+cudaError_t launch_reduce_3d(Solver& s);
+
+// Deterministic final sum of the per-block partials (islbm_d2.cu).
+cudaError_t launch_finish_reduce(Solver& s);
+
+}  // namespace islbm
+
+// The opaque handle of the C ABI is the solver itself.
+struct islbm_solver : public islbm::Solver {};

@@ -1,0 +1,377 @@
+"""ctypes binding of libislbm (include/islbm.h).
+
+The functions below carry the names of the C entry points and only marshal
+arguments: numpy arrays for host buffers, torch CUDA tensors (or raw device
+addresses) for device buffers, and torch's current CUDA stream by default.
+Every computation runs in the library's CUDA kernels; there is no CPU path.
+If the library has not been built the first call raises ``IslbmError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LATTICES = {"d2q9_d2q5": 0, "d3q19_d3q7": 1}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp16dev": 2, "bf16dev": 3}
+STENCILS = {"centred": 0, "upwind": 1}
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_DIVERGED",
+          5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_IO"}
+
+# symbols declared in include/islbm.h
+EXPORTS = (
+    "islbm_mesh_uniform", "islbm_mesh_erf", "islbm_mesh_tanh", "islbm_default_params",
+    "islbm_create", "islbm_destroy", "islbm_last_error", "islbm_info",
+    "islbm_set_fields", "islbm_set_fields_device", "islbm_set_populations", "islbm_step",
+    "islbm_get_fields", "islbm_get_fields_device", "islbm_get_populations", "islbm_reduce",
+    "islbm_nusselt", "islbm_reynolds", "islbm_mass", "islbm_synchronize", "islbm_save",
+    "islbm_load",
+)
+
+
+class IslbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"islbm {STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("Ma", ctypes.c_double), ("T_hot", ctypes.c_double), ("T_cold", ctypes.c_double),
+                ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
+                ("s_pi", ctypes.c_double), ("s_m", ctypes.c_double), ("q_j", ctypes.c_double),
+                ("q_e", ctypes.c_double), ("q_nu", ctypes.c_double), ("stencil", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("q_flow", ctypes.c_int),
+                ("q_temp", ctypes.c_int), ("uniform", ctypes.c_int), ("precision", ctypes.c_int),
+                ("L", ctypes.c_double), ("u_f", ctypes.c_double), ("nu", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("gbeta", ctypes.c_double), ("s_nu", ctypes.c_double),
+                ("a_T", ctypes.c_double), ("omega", ctypes.c_double),
+                ("steps_per_tf", ctypes.c_double), ("bytes_per_update", ctypes.c_double),
+                ("time", ctypes.c_longlong)]
+
+
+class Reductions(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("Nu", "Nu_hot", "Nu_cold", "Nu_middle", "Re", "Re_uv", "mass", "ke",
+                 "max_speed", "nonfinite")] + [("time", ctypes.c_longlong)]
+
+
+class NuOut(ctypes.Structure):
+    _fields_ = [("vol", ctypes.c_double), ("hot", ctypes.c_double), ("cold", ctypes.c_double),
+                ("middle", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libislbm.so (optionally building it first).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise IslbmError(2, f"{path} is not built; run paper_2509_01099_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    d, i, vp, h = ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p
+    dp = P(ctypes.c_double)
+    sig = {
+        "islbm_mesh_uniform": (i, [i, dp]),
+        "islbm_mesh_erf": (i, [i, d, dp]),
+        "islbm_mesh_tanh": (i, [i, d, dp]),
+        "islbm_default_params": (None, [P(Params)]),
+        "islbm_create": (i, [dp, i, dp, i, dp, i, d, d, i, i, P(Params), vp, P(h)]),
+        "islbm_destroy": (None, [h]),
+        "islbm_last_error": (ctypes.c_char_p, [h]),
+        "islbm_info": (i, [h, P(Info)]),
+        "islbm_set_fields": (i, [h, dp, dp, dp, dp, dp]),
+        "islbm_set_fields_device": (i, [h, vp, vp, vp, vp, vp]),
+        "islbm_set_populations": (i, [h, dp, dp]),
+        "islbm_step": (i, [h, ctypes.c_longlong]),
+        "islbm_get_fields": (i, [h, dp, dp, dp, dp, dp]),
+        "islbm_get_fields_device": (i, [h, vp, vp, vp, vp, vp]),
+        "islbm_get_populations": (i, [h, dp, dp]),
+        "islbm_reduce": (i, [h, P(Reductions)]),
+        "islbm_nusselt": (i, [h, P(NuOut)]),
+        "islbm_reynolds": (i, [h, dp]),
+        "islbm_mass": (i, [h, dp]),
+        "islbm_synchronize": (i, [h]),
+        "islbm_save": (i, [h, ctypes.c_char_p]),
+        "islbm_load": (i, [h, ctypes.c_char_p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, handle=None):
+    if st != 0:
+        msg = load_library().islbm_last_error(handle)
+        raise IslbmError(st, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    """Host double pointer of a C-contiguous float64 array (or None)."""
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _host(a, n):
+    if a is None:
+        return None
+    arr = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if arr.size != n:
+        raise ValueError(f"expected {n} values, got {arr.size}")
+    return arr
+
+
+def _devptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    return t.data_ptr()
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# functions named as the C entry points
+# ---------------------------------------------------------------------------
+
+def islbm_mesh_uniform(n: int) -> np.ndarray:
+    xi = np.empty(n + 2)
+    _check(load_library().islbm_mesh_uniform(n, _dptr(xi)))
+    return xi
+
+
+def islbm_mesh_erf(n: int, a: float = 1.5) -> np.ndarray:
+    xi = np.empty(n + 2)
+    _check(load_library().islbm_mesh_erf(n, a, _dptr(xi)))
+    return xi
+
+
+def islbm_mesh_tanh(n: int, a: float = 1.5) -> np.ndarray:
+    xi = np.empty(n + 2)
+    _check(load_library().islbm_mesh_tanh(n, a, _dptr(xi)))
+    return xi
+
+
+def islbm_default_params() -> Params:
+    p = Params()
+    load_library().islbm_default_params(ctypes.byref(p))
+    return p
+
+
+def islbm_create(xi_x, xi_y, xi_z=None, Ra=1e6, Pr=0.71, lattice=None, precision="fp32",
+                 params: Params | None = None, stream=None):
+    lib = load_library()
+    if lattice is None:
+        lattice = "d2q9_d2q5" if xi_z is None else "d3q19_d3q7"
+    xs = [np.ascontiguousarray(x, dtype=np.float64) if x is not None else None
+          for x in (xi_x, xi_y, xi_z)]
+    ns = [len(x) - 2 if x is not None else 0 for x in xs]
+    h = ctypes.c_void_p()
+    if stream is None:
+        stream = _current_stream()
+    st = lib.islbm_create(_dptr(xs[0]), ns[0], _dptr(xs[1]), ns[1], _dptr(xs[2]), ns[2],
+                          float(Ra), float(Pr), LATTICES[lattice], PRECISIONS[precision],
+                          ctypes.byref(params) if params is not None else None,
+                          stream, ctypes.byref(h))
+    _check(st)
+    return h
+
+
+def islbm_destroy(h):
+    load_library().islbm_destroy(h)
+
+
+def islbm_info(h) -> Info:
+    o = Info()
+    _check(load_library().islbm_info(h, ctypes.byref(o)), h)
+    return o
+
+
+def islbm_set_fields(h, T, u=None, v=None, w=None, rho=None, nodes=None):
+    n = nodes if nodes is not None else int(np.asarray(T).size)
+    arrs = [_host(a, n) for a in (rho, T, u, v, w)]
+    _check(load_library().islbm_set_fields(h, *[_dptr(a) for a in arrs]), h)
+
+
+def islbm_set_fields_device(h, T, u=None, v=None, w=None, rho=None):
+    _check(load_library().islbm_set_fields_device(h, *[_devptr(a) for a in (rho, T, u, v, w)]), h)
+
+
+def islbm_set_populations(h, f, g):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    _check(load_library().islbm_set_populations(h, _dptr(f), _dptr(g)), h)
+
+
+def islbm_step(h, n: int = 1):
+    _check(load_library().islbm_step(h, int(n)), h)
+
+
+def islbm_get_fields(h, shape, with_w=False):
+    nodes = int(np.prod(shape))
+    out = {k: np.empty(nodes) for k in ("rho", "T", "u", "v")}
+    if with_w:
+        out["w"] = np.empty(nodes)
+    _check(load_library().islbm_get_fields(h, _dptr(out["rho"]), _dptr(out["T"]), _dptr(out["u"]),
+                                           _dptr(out["v"]), _dptr(out.get("w"))), h)
+    return {k: a.reshape(shape) for k, a in out.items()}
+
+
+def islbm_get_fields_device(h, rho=None, T=None, u=None, v=None, w=None):
+    _check(load_library().islbm_get_fields_device(h, *[_devptr(a) for a in (rho, T, u, v, w)]), h)
+
+
+def islbm_get_populations(h, q_flow, q_temp, shape):
+    nodes = int(np.prod(shape))
+    f = np.empty((q_flow, nodes))
+    g = np.empty((q_temp, nodes))
+    _check(load_library().islbm_get_populations(h, _dptr(f), _dptr(g)), h)
+    return f.reshape((q_flow,) + tuple(shape)), g.reshape((q_temp,) + tuple(shape))
+
+
+def islbm_reduce(h, check: bool = True) -> dict:
+    r = Reductions()
+    st = load_library().islbm_reduce(h, ctypes.byref(r))
+    if check:
+        _check(st, h)
+    out = {k: getattr(r, k) for k, _ in Reductions._fields_}
+    out["status"] = st
+    return out
+
+
+def islbm_nusselt(h) -> dict:
+    o = NuOut()
+    _check(load_library().islbm_nusselt(h, ctypes.byref(o)), h)
+    return {"vol": o.vol, "hot": o.hot, "cold": o.cold, "middle": o.middle}
+
+
+def islbm_reynolds(h) -> float:
+    x = ctypes.c_double()
+    _check(load_library().islbm_reynolds(h, ctypes.byref(x)), h)
+    return x.value
+
+
+def islbm_mass(h) -> float:
+    x = ctypes.c_double()
+    _check(load_library().islbm_mass(h, ctypes.byref(x)), h)
+    return x.value
+
+
+def islbm_synchronize(h):
+    _check(load_library().islbm_synchronize(h), h)
+
+
+def islbm_save(h, path: str):
+    _check(load_library().islbm_save(h, path.encode()), h)
+
+
+def islbm_load(h, path: str):
+    _check(load_library().islbm_load(h, path.encode()), h)
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Solver:
+    """One cavity solver handle; methods map one-to-one onto the C entry points."""
+
+    def __init__(self, xi_x, xi_y, xi_z=None, Ra=1e6, Pr=0.71, precision="fp32",
+                 params: Params | None = None, stream=None, **overrides):
+        if overrides:
+            params = params if params is not None else islbm_default_params()
+            for k, v in overrides.items():
+                setattr(params, k, STENCILS[v] if k == "stencil" and isinstance(v, str) else v)
+        self.h = islbm_create(xi_x, xi_y, xi_z, Ra, Pr, None, precision, params, stream)
+        self.info = islbm_info(self.h)
+        self.dim = self.info.dim
+        n = list(self.info.n)
+        self.shape = (n[1], n[0]) if self.dim == 2 else (n[2], n[1], n[0])
+
+    def close(self):
+        if getattr(self, "h", None):
+            islbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def time(self) -> int:
+        return islbm_info(self.h).time
+
+    def set_fields(self, T, u=None, v=None, w=None, rho=None):
+        islbm_set_fields(self.h, T, u, v, w, rho, nodes=int(np.prod(self.shape)))
+
+    def set_fields_device(self, T, u=None, v=None, w=None, rho=None):
+        islbm_set_fields_device(self.h, T, u, v, w, rho)
+
+    def set_populations(self, f, g):
+        islbm_set_populations(self.h, f, g)
+
+    def step(self, n: int = 1):
+        islbm_step(self.h, n)
+
+    def fields(self) -> dict:
+        return islbm_get_fields(self.h, self.shape, with_w=self.dim == 3)
+
+    def fields_device(self, rho=None, T=None, u=None, v=None, w=None):
+        islbm_get_fields_device(self.h, rho, T, u, v, w)
+
+    def populations(self):
+        return islbm_get_populations(self.h, self.info.q_flow, self.info.q_temp, self.shape)
+
+    def reduce(self, check: bool = True) -> dict:
+        return islbm_reduce(self.h, check)
+
+    def synchronize(self):
+        islbm_synchronize(self.h)
+
+    def save(self, path):
+        islbm_save(self.h, path)
+
+    def load(self, path):
+        islbm_load(self.h, path)

@@ -1,0 +1,93 @@
+"""The C-ABI library: it builds, loads, exports every declared entry point, and its
+host-side set-up agrees with the oracle.  No kernel is launched here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2509_01099_gb300 as pkg
+from paper_2509_01099_gb300 import build as B
+from oracle import islbm_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return pkg.load_library()
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "islbm.h")).read()
+    return sorted(set(re.findall(r"ISLBM_API\s+[\w\s\*]*?\b(islbm_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(pkg.EXPORTS)
+
+
+@pytest.mark.parametrize("n", [4, 5, 64, 257, 1024])
+def test_mesh_helpers_match_the_oracle(lib, n):
+    np.testing.assert_allclose(pkg.islbm_mesh_erf(n, 1.5), O.mesh_erf(n, 1.5), rtol=0, atol=2e-16)
+    np.testing.assert_allclose(pkg.islbm_mesh_tanh(n, 1.5), O.mesh_tanh(n, 1.5), rtol=0, atol=2e-16)
+    np.testing.assert_allclose(pkg.islbm_mesh_uniform(n), O.mesh_uniform(n), rtol=0, atol=2e-16)
+    xi = pkg.islbm_mesh_erf(n, 2.1)
+    np.testing.assert_array_equal(xi + xi[::-1], np.ones_like(xi))
+
+
+def test_mesh_helpers_reject_bad_arguments(lib):
+    with pytest.raises(pkg.IslbmError):
+        pkg.islbm_mesh_erf(3, 1.5)
+    with pytest.raises(pkg.IslbmError):
+        pkg.islbm_mesh_tanh(16, -1.0)
+
+
+def test_default_params(lib):
+    p = pkg.islbm_default_params()
+    assert p.Ma == 0.1 and p.T_hot == 0.5 and p.T_cold == -0.5 and p.stencil == 0
+
+
+def _create(xi_x, xi_y, **kw):
+    return pkg.islbm_create(xi_x, xi_y, None, kw.pop("Ra", 1e6), 0.71, None, "fp32", None, None)
+
+
+def test_create_validates_meshes_before_touching_a_device(lib):
+    good = O.mesh_erf(16, 1.5)
+    bad = good.copy()
+    bad[5], bad[6] = bad[6], bad[5]                      # not increasing
+    with pytest.raises(pkg.IslbmError) as e:
+        _create(bad, good)
+    assert e.value.status == 1
+    with pytest.raises(pkg.IslbmError) as e:
+        _create(O.mesh_erf(16, 1.5), O.mesh_erf(24, 1.5))  # different lattice units
+    assert e.value.status == 1
+    lopsided = good.copy()
+    lopsided[-1] += 0.01                                  # ghost spacing differs at the ends
+    with pytest.raises(pkg.IslbmError) as e:
+        _create(lopsided, good)
+    assert e.value.status == 1
+
+
+def test_no_cpu_fallback_without_a_gpu(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    xi = O.mesh_erf(16, 1.5)
+    with pytest.raises(pkg.IslbmError) as e:
+        _create(xi, xi)
+    assert e.value.status == 2                            # ISLBM_ERR_CUDA, loudly
+
+
+def test_diffusivity_range_is_checked(lib):
+    # tiny Ra on a coarse mesh gives alpha beyond the D2Q5 range (a_T > 1)
+    xi = O.mesh_uniform(8)
+    with pytest.raises(pkg.IslbmError) as e:
+        _create(xi, xi, Ra=1e-4)
+    assert e.value.status == 1

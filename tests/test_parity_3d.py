@@ -1,0 +1,82 @@
+"""GPU parity of the 3-D CUDA path (D3Q19 + D3Q7) against the FP64 oracle.
+
+Tolerances as in the 2-D tests: field-relative 1e-11 (FP64) and 1e-5 (FP32).
+"""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import islbm_oracle as O
+from synthetic import random_populations, random_signed, temperature_noise
+from tests.helpers import gpu_available, rel_field_error
+
+pytestmark = pytest.mark.gpu
+
+if gpu_available():
+    from paper_2509_01099_gb300 import build as _B
+    _B.build()
+import paper_2509_01099_gb300 as pkg  # noqa: E402
+
+MESHES = {
+    "erf14": lambda: (O.mesh_erf(14, 1.5),) * 3,
+    "tanh16": lambda: (O.mesh_tanh(16, 1.5),) * 3,
+    # ragged box of unit spacings: 11 x 9 x 7 nodes (height 9)
+    "uniform11x9x7": lambda: ((np.arange(13) - 0.5) / 9, O.mesh_uniform(9),
+                              (np.arange(9) - 0.5) / 9),
+}
+TOL = {"fp64": 1e-11, "fp32": 1e-5}
+NU_TOL = {"fp64": 1e-10, "fp32": 1e-4}
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_run(mesh, Ra, steps):
+    xi = MESHES[mesh]()
+    cav = O.Cavity(*xi, params=O.Params(Ra=Ra))
+    cav.init_fields(temperature_noise(cav.shape, 1e-6, seed=0))
+    cav.step(steps)
+    rho, u, T = cav.fields()
+    return {"rho": rho, "u": u[0], "v": u[1], "w": u[2], "T": T, "red": cav.reductions()}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("mesh", list(MESHES))
+def test_cavity_fields_3d(mesh, precision):
+    steps = 300
+    ref = oracle_run(mesh, 1e6, steps)
+    xi = MESHES[mesh]()
+    s = pkg.Solver(*xi, Ra=1e6, precision=precision)
+    s.set_fields(temperature_noise(s.shape, 1e-6, seed=0))
+    s.step(steps)
+    got = s.fields()
+    red = s.reduce()
+    s.close()
+    for k in ("T", "u", "v", "w"):
+        assert rel_field_error(got[k], ref[k]) <= TOL[precision], k
+    for k in ("Nu", "Nu_hot", "Nu_cold", "Re", "Re_uv"):
+        r = abs(red[k] - ref["red"][k]) / abs(ref["red"][k])
+        assert r <= NU_TOL[precision], (k, red[k], ref["red"][k])
+    assert np.isnan(red["Nu_middle"])
+
+
+POP_TOL = {"fp64": 1e-13, "fp32": 2e-6, "fp16dev": 2e-3, "bf16dev": 2e-2}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16dev", "bf16dev"])
+@pytest.mark.parametrize("mesh", ["erf14", "uniform11x9x7"])
+@pytest.mark.parametrize("steps", [0, 1, 3])
+def test_random_state_populations_3d(mesh, precision, steps):
+    xi = MESHES[mesh]()
+    cav = O.Cavity(*xi, params=O.Params(Ra=1e6))
+    f = random_populations(19, cav.shape, seed=21, spread=0.2)
+    g = random_signed(7, cav.shape, seed=22, amplitude=0.08)
+    cav.init_populations(f, g)
+    cav.step(steps)
+    fp_ref, gp_ref = cav.post_collision()
+    s = pkg.Solver(*xi, Ra=1e6, precision=precision)
+    s.set_populations(f, g)
+    s.step(steps)
+    fp, gp = s.populations()
+    s.close()
+    assert np.abs(fp - fp_ref).max() / np.abs(fp_ref).max() <= POP_TOL[precision]
+    assert np.abs(gp - gp_ref).max() / np.abs(gp_ref).max() <= POP_TOL[precision]
