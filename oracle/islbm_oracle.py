@@ -626,7 +626,8 @@ class Cavity:
     def reductions(self):
         """<Nu>, Nu_hot, Nu_cold, Nu_middle (2-D), <Re>, mass, kinetic energy (Sec. 3, Sec. 4).
 
-        <phi>_V = sum phi prod W / L^d (Eq. (18) on every axis); u* = u/u_f,
+        <phi>_V = sum phi prod W / sum prod W (Eq. (18) on every axis, divided by
+        the cavity volume, L^d for the square cavity); u* = u/u_f,
         T* = (T - T0)/dT with dT = T_hot - T_cold; x* = X/L.
         """
         rho, u, T = self.fields()
@@ -635,7 +636,7 @@ class Cavity:
         Ts = (T - p.T0) / dT
         us = [c / par.u_f for c in u]
         Wv = self.volume_weights()
-        vol = L ** d
+        vol = float(Wv.sum())           # L^d for the square / cubic cavity
         out = {}
         out["Nu"] = math.sqrt(p.Ra * p.Pr) * float((Wv * us[0] * Ts).sum()) / vol + 1.0
         speed = np.sqrt(sum(c * c for c in us))
@@ -651,7 +652,7 @@ class Cavity:
             shape = [1] * (d - 1)
             shape[d - 1 - a] = len(self.W[a])
             Wp = Wp * self.W[a].reshape(shape)
-        area = L ** (d - 1)
+        area = float(Wp.sum())          # L^(d-1) for the square / cubic cavity
         # Nu = -<dT*/dx*>, dT*/dx* = (L/dT) dT/dX
         for side in ("hot", "cold"):
             dTdX = self.wall_derivative(T, side)

@@ -114,8 +114,16 @@ unsigned long long fnv(const void* data, size_t n, unsigned long long h) {
 islbm_status finish_reductions(Solver* s, islbm_reductions* out) {
   const double* r = s->hresult;
   const Physics& h = s->ph;
-  const double L = h.L, d = s->dim;
-  const double vol = std::pow(L, d), area = std::pow(L, d - 1);
+  const double L = h.L;
+  // the averages divide by the measure of the cavity and of a side wall
+  // (L^d and L^(d-1) for the square / cubic cavity)
+  double vol = 1.0, area = 1.0;
+  for (int a = 0; a < s->dim; ++a) {
+    const Axis& A = s->ax[a];
+    const double La = A.X[A.n] - A.X[1] + 1.0;
+    vol *= La;
+    if (a > 0) area *= La;
+  }
   const double dT = h.dT;
   islbm_reductions o;
   std::memset(&o, 0, sizeof(o));

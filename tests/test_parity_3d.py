@@ -1,6 +1,13 @@
 """GPU parity of the 3-D CUDA path (D3Q19 + D3Q7) against the FP64 oracle.
 
-Tolerances as in the 2-D tests: field-relative 1e-11 (FP64) and 1e-5 (FP32).
+Tolerances as in the 2-D tests: 1e-11 (FP64) and 1e-5 (FP32) relative to the
+field's largest value, with the velocity measured as one vector field (the
+spanwise component w is ~1e-2 of u early in a run, so normalising it by
+itself would amplify rounding by 1e2).  Far-from-equilibrium population
+states accumulate about 3 steps x 50 operations of rounding: bounds 1e-13
+(FP64), 5e-6 (FP32, unit roundoff 6e-8), 5e-3 (FP16 storage of deviations,
+2^-11 relative) and 5e-2 (BF16 storage, 2^-8 relative), relative to the
+largest population.
 """
 import functools
 
@@ -9,7 +16,7 @@ import pytest
 
 from oracle import islbm_oracle as O
 from synthetic import random_populations, random_signed, temperature_noise
-from tests.helpers import gpu_available, rel_field_error
+from tests.helpers import gpu_available, rel_field_error, rel_vector_error
 
 pytestmark = pytest.mark.gpu
 
@@ -42,7 +49,7 @@ def oracle_run(mesh, Ra, steps):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("mesh", list(MESHES))
 def test_cavity_fields_3d(mesh, precision):
-    steps = 300
+    steps = 1000
     ref = oracle_run(mesh, 1e6, steps)
     xi = MESHES[mesh]()
     s = pkg.Solver(*xi, Ra=1e6, precision=precision)
@@ -51,15 +58,16 @@ def test_cavity_fields_3d(mesh, precision):
     got = s.fields()
     red = s.reduce()
     s.close()
-    for k in ("T", "u", "v", "w"):
-        assert rel_field_error(got[k], ref[k]) <= TOL[precision], k
+    assert rel_field_error(got["T"], ref["T"]) <= TOL[precision]
+    err_u = rel_vector_error([got[k] for k in "uvw"], [ref[k] for k in "uvw"])
+    assert err_u <= TOL[precision], err_u
     for k in ("Nu", "Nu_hot", "Nu_cold", "Re", "Re_uv"):
         r = abs(red[k] - ref["red"][k]) / abs(ref["red"][k])
         assert r <= NU_TOL[precision], (k, red[k], ref["red"][k])
     assert np.isnan(red["Nu_middle"])
 
 
-POP_TOL = {"fp64": 1e-13, "fp32": 2e-6, "fp16dev": 2e-3, "bf16dev": 2e-2}
+POP_TOL = {"fp64": 1e-13, "fp32": 5e-6, "fp16dev": 5e-3, "bf16dev": 5e-2}
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16dev", "bf16dev"])
