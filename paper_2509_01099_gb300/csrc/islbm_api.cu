@@ -332,6 +332,7 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
     tab_bytes += 2 * (((size_t)n * 4 + 255) / 256 * 256);
     tab_bytes += 2 * (((size_t)3 * n * rsize + 255) / 256 * 256);
     tab_bytes += ((size_t)n * 8 + 255) / 256 * 256;
+    tab_bytes += 2 * (((size_t)n * 16 + 255) / 256 * 256);
   }
   tab_bytes += 256;
   s->red_blocks = 4 * 152;
@@ -381,6 +382,23 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
     std::memcpy(host.data() + off, A.W.data(), (size_t)n * 8);
     s->dax[a].W = reinterpret_cast<const double*>(dbase + off);
     off += (size_t)n * 8;
+    // packed FP32 tables of the tiled kernels: wall entries get zero weights
+    // and a stencil base inside the axis
+    for (int k = 0; k < 2; ++k) {
+      off = (off + 255) & ~size_t(255);
+      for (int j = 0; j < n; ++j) {
+        int b = A.base[k][j];
+        float w4[4] = {(float)A.w[k][3 * j], (float)A.w[k][3 * j + 1], (float)A.w[k][3 * j + 2], 0.f};
+        if (b < 0) {
+          b = std::min(std::max(j - 1, 0), n - 3);
+          w4[0] = w4[1] = w4[2] = 0.f;
+        }
+        std::memcpy(&w4[3], &b, 4);
+        std::memcpy(host.data() + off + (size_t)j * 16, w4, 16);
+      }
+      s->dax[a].packed[k] = reinterpret_cast<const float4*>(dbase + off);
+      off += (size_t)n * 16;
+    }
   }
   e = cudaMemcpyAsync(s->dtables, host.data(), tab_bytes, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) return cleanup(ISLBM_ERR_CUDA, "islbm_create: table upload");

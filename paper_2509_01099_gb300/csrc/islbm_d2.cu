@@ -12,6 +12,7 @@
 // which is the paper's collide -> stream -> interpolate cycle with the state
 // stored after the collision instead of before it.
 #include <cstdint>
+#include <type_traits>
 
 #include "islbm_internal.h"
 #include "islbm_store.cuh"
@@ -27,6 +28,8 @@ struct P2 {
   const R* wx[2];
   const int* by[2];
   const R* wy[2];
+  const float4* px[2];  // packed FP32 tables of the tiled kernel
+  const float4* py[2];
   R gbeta, T0, s_e, s_eps, s_q, s_nu, q_j, q_e, q_nu, a_T;
   R abb_hot, abb_cold;  // omega (T_w - T0) of the anti-bounce-back rule
 };
@@ -403,6 +406,8 @@ P2<R> make_params(const Solver& s) {
     p.wx[k] = static_cast<const R*>(s.dax[0].w[k]);
     p.by[k] = s.dax[1].base[k];
     p.wy[k] = static_cast<const R*>(s.dax[1].w[k]);
+    p.px[k] = s.dax[0].packed[k];
+    p.py[k] = s.dax[1].packed[k];
   }
   const Physics& h = s.ph;
   p.gbeta = R(h.gbeta);
@@ -418,6 +423,230 @@ P2<R> make_params(const Solver& s) {
   p.abb_hot = R(h.omega * (h.T_hot - h.T0));
   p.abb_cold = R(h.omega * (h.T_cold - h.T0));
   return p;
+}
+
+
+// ---------------------------------------------------------------------------
+// Tiled step (FP32 compute, any 32/16-bit storage, centred stencil).
+//
+// A CTA owns a 64 x (4R) tile.  All 14 population planes of the tile plus a
+// one-node halo (rounded out to a 16-byte chunk in x) are staged in shared
+// memory with cp.async, so every global value is fetched once by a coalesced
+// 16-byte copy.  Thread (c, rg) owns column c and the R rows rg*R .. rg*R+R-1:
+// the quadratic interpolation is applied axis by axis (Sec. 2.2): R+2 rows are
+// interpolated in x once and reused by the R outputs of the y pass.  Tiles that
+// touch a y-wall take the general per-node path.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+constexpr int kTX = 64;       // tile width
+constexpr int kRG = 4;        // row groups per tile
+constexpr int kThreads = kTX * kRG;
+
+template <typename S, int R>
+struct TileGeom {
+  static constexpr int TY = R * kRG;
+  static constexpr int HX = 16 / (int)sizeof(S);      // halo columns: one 16-byte chunk
+  static constexpr int SW = kTX + 2 * HX;              // staged row width
+  static constexpr int SH = TY + 2;                    // staged rows
+  static constexpr int CPR = SW / HX;                  // chunks per staged row
+  static constexpr int PLANE = SH * SW;                // staged elements per population
+  static constexpr size_t smem_bytes() {
+    return (size_t)14 * PLANE * sizeof(S) + (size_t)2 * TY * sizeof(float4);
+  }
+};
+
+template <typename S, int R, bool UNI>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_step_tiled(const S* __restrict__ fin, S* __restrict__ fout, P2<float> p) {
+  using G = TileGeom<S, R>;
+  constexpr int TY = G::TY, HX = G::HX, SW = G::SW, SH = G::SH, CPR = G::CPR;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* sm = reinterpret_cast<S*>(smem_raw);
+  float4* wyt = reinterpret_cast<float4*>(smem_raw + (size_t)14 * G::PLANE * sizeof(S));
+
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
+  const int cx0 = x0 - HX;
+  const int ry0 = max(0, min(y0 - 1, p.ny - 3));
+  // ---- stage the tile + halo of every plane ----
+  constexpr int CPP = SH * CPR;
+  for (int k = threadIdx.x; k < 14 * CPP; k += kThreads) {
+    const int pl = k / CPP;
+    const int r = k - pl * CPP;
+    const int row = r / CPR;
+    const int ch = r - row * CPR;
+    const int gy = ry0 + row, gx = cx0 + ch * HX;
+    const bool ok = gy < p.ny && gx >= 0 && gx + HX <= p.pitch;
+    const S* src = ok ? fin + (size_t)pl * p.plane + (size_t)gy * p.pitch + gx : fin;
+    cp_async16(sm + (size_t)pl * G::PLANE + row * SW + ch * HX, src, ok);
+  }
+  if (!UNI && threadIdx.x < 2 * TY) {
+    const int k = threadIdx.x / TY, yy = y0 + threadIdx.x % TY;
+    wyt[threadIdx.x] = yy < p.ny ? __ldg(p.py[k] + yy) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  const int c = threadIdx.x % kTX, rg = threadIdx.x / kTX;
+  const int x = x0 + c;
+  if (x >= p.nx) return;
+  const int col = x - cx0;
+  const bool wW = (x == 0), wE = (x == p.nx - 1);
+  float4 tp = make_float4(0.f, 0.f, 0.f, 0.f), tm = tp;
+  int bp = col - 1, bm = col - 1;
+  if (!UNI) {
+    tp = __ldg(p.px[0] + x);
+    tm = __ldg(p.px[1] + x);
+    bp = __float_as_int(tp.w) - cx0;
+    bm = __float_as_int(tm.w) - cx0;
+  }
+  auto rd = [&](int pl, int row, int cl) -> float {
+    return to_f(sm[(size_t)pl * G::PLANE + row * SW + cl]);
+  };
+  // x-interpolated value of plane pl in staged row `row` for direction cx
+  auto xi = [&](int pl, int row, int cx) -> float {
+    if (UNI) return rd(pl, row, col - cx);
+    const float4 t = cx > 0 ? tp : tm;
+    const int b = cx > 0 ? bp : bm;
+    return t.x * rd(pl, row, b) + t.y * rd(pl, row, b + 1) + t.z * rd(pl, row, b + 2);
+  };
+
+  const int yr0 = y0 + rg * R;            // first output row of the thread
+  const int lr0 = yr0 - ry0;              // its staged row
+  const bool fast = (y0 >= 1) && (y0 + TY <= p.ny - 1);
+  float f[9][R], g[5][R];
+
+  if (fast) {
+    // rows yr0-1 .. yr0+R are staged rows lr0-1 .. lr0+R
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int lr = lr0 + m;
+      f[0][m] = rd(0, lr, col);
+      g[0][m] = rd(9, lr, col);
+      f[1][m] = wW ? rd(3, lr, col) : xi(1, lr, +1);
+      f[3][m] = wE ? rd(1, lr, col) : xi(3, lr, -1);
+      g[1][m] = wW ? p.abb_hot - rd(12, lr, col) : xi(10, lr, +1);
+      g[3][m] = wE ? p.abb_cold - rd(10, lr, col) : xi(12, lr, -1);
+    }
+    // planes moving in y: window of R+2 (x-interpolated) rows, then the y pass
+    auto ypass = [&](int pl, int cx, int cy, float (&out)[R]) {
+      float h[R + 2];
+#pragma unroll
+      for (int l = 0; l < R + 2; ++l) h[l] = (cx == 0) ? rd(pl, lr0 - 1 + l, col) : xi(pl, lr0 - 1 + l, cx);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        if (UNI) {
+          out[m] = h[m + 1 - cy];
+        } else {
+          const float4 q = wyt[(cy > 0 ? 0 : TY) + rg * R + m];
+          out[m] = q.x * h[m] + q.y * h[m + 1] + q.z * h[m + 2];
+        }
+      }
+    };
+    ypass(2, 0, +1, f[2]);
+    ypass(4, 0, -1, f[4]);
+    ypass(5, +1, +1, f[5]);
+    ypass(6, -1, +1, f[6]);
+    ypass(7, -1, -1, f[7]);
+    ypass(8, +1, -1, f[8]);
+    ypass(11, 0, +1, g[2]);
+    ypass(13, 0, -1, g[4]);
+    // half-way bounce-back where the departure point lies behind an x-wall
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int lr = lr0 + m;
+      if (wW) {
+        f[5][m] = rd(7, lr, col);
+        f[8][m] = rd(6, lr, col);
+      }
+      if (wE) {
+        f[6][m] = rd(8, lr, col);
+        f[7][m] = rd(5, lr, col);
+      }
+    }
+  } else {
+    // general path: y-walls and clamped stencils, node by node
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int y = yr0 + m;
+      const int lr = y - ry0;
+      if (y >= p.ny) break;
+      const bool wS = (y == 0), wN = (y == p.ny - 1);
+      const float4 qp = wyt[rg * R + m], qm = wyt[TY + rg * R + m];
+      const int brp = UNI ? lr - 1 : __float_as_int(qp.w) - ry0;
+      const int brm = UNI ? lr + 1 - 2 : __float_as_int(qm.w) - ry0;
+      auto ypull = [&](int pl, int cx, int cy) -> float {
+        if (UNI) return (cx == 0) ? rd(pl, lr - cy, col) : xi(pl, lr - cy, cx);
+        const float4 q = cy > 0 ? qp : qm;
+        const int br = cy > 0 ? brp : brm;
+        if (cx == 0) return q.x * rd(pl, br, col) + q.y * rd(pl, br + 1, col) + q.z * rd(pl, br + 2, col);
+        return q.x * xi(pl, br, cx) + q.y * xi(pl, br + 1, cx) + q.z * xi(pl, br + 2, cx);
+      };
+      f[0][m] = rd(0, lr, col);
+      g[0][m] = rd(9, lr, col);
+      f[1][m] = wW ? rd(3, lr, col) : xi(1, lr, +1);
+      f[3][m] = wE ? rd(1, lr, col) : xi(3, lr, -1);
+      f[2][m] = wS ? rd(4, lr, col) : ypull(2, 0, +1);
+      f[4][m] = wN ? rd(2, lr, col) : ypull(4, 0, -1);
+      f[5][m] = (wW || wS) ? rd(7, lr, col) : ypull(5, +1, +1);
+      f[6][m] = (wE || wS) ? rd(8, lr, col) : ypull(6, -1, +1);
+      f[7][m] = (wE || wN) ? rd(5, lr, col) : ypull(7, -1, -1);
+      f[8][m] = (wW || wN) ? rd(6, lr, col) : ypull(8, +1, -1);
+      g[1][m] = wW ? p.abb_hot - rd(12, lr, col) : xi(10, lr, +1);
+      g[3][m] = wE ? p.abb_cold - rd(10, lr, col) : xi(12, lr, -1);
+      g[2][m] = wS ? rd(13, lr, col) : ypull(11, 0, +1);
+      g[4][m] = wN ? rd(11, lr, col) : ypull(13, 0, -1);
+    }
+  }
+
+  // ---- collide and store ----
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    const int y = yr0 + m;
+    if (y >= p.ny) break;
+    float fn[9], gn[5];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fn[i] = f[i][m];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) gn[i] = g[i][m];
+    float rho, ux, uy, T;
+    collide(fn, gn, p, rho, ux, uy, T);
+    const size_t idx = (size_t)y * p.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<S>::st(fout + (size_t)i * p.plane + idx, fn[i]);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Store<S>::st(fout + (size_t)(9 + i) * p.plane + idx, gn[i]);
+  }
+}
+
+template <typename S, int R, bool UNI>
+cudaError_t launch_tiled(const Solver& s, const S* in, S* out, const P2<float>& p) {
+  using G = TileGeom<S, R>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_step_tiled<S, R, UNI>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)G::smem_bytes());
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const dim3 grid((s.n[0] + kTX - 1) / kTX, (s.n[1] + G::TY - 1) / G::TY);
+  k_step_tiled<S, R, UNI><<<grid, kThreads, G::smem_bytes(), s.stream>>>(in, out, p);
+  return cudaGetLastError();
 }
 
 dim3 block2() { return dim3(32, 8); }
@@ -442,6 +671,12 @@ struct StepFn {
     const P2<R> p = make_params<R>(s);
     const S* in = static_cast<const S*>(s.buf[s.cur]);
     S* out = static_cast<S*>(s.buf[s.cur ^ 1]);
+    if constexpr (!std::is_same<S, double>::value) {
+      // the tiled kernel covers the centred stencil (its halo is one node)
+      // (on the uniform mesh the direct pure-shift kernel is faster)
+      if (s.stencil == ISLBM_STENCIL_CENTRED && !s.uniform)
+        return launch_tiled<S, 4, false>(s, in, out, p);
+    }
     if (s.uniform)
       k_step<S, true><<<grid2(s), block2(), 0, s.stream>>>(in, out, p);
     else

@@ -46,6 +46,7 @@ struct DevAxis {
   const int* base[2];
   const void* w[2];
   const double* W;
+  const float4* packed[2];  // FP32 (w0, w1, w2, base as int bits); walls: zero weights
 };
 
 // Lattice-unit physics of a handle.
