@@ -6,7 +6,8 @@ Workload (default): the 2-D side-heated cavity at Ra = 1e8, Pr = 0.71 on a
 storage.  One bench step is one full ISLBM time step of the whole cavity
 (virtual streaming + quadratic interpolation + walls + MRT collision, one fused
 kernel).  The timed region holds exactly K steps; before each timed step a
-256 MB buffer is written to flush the 126 MB L2, and each step is bracketed
+256 MB buffer is written to flush the 126 MB L2 (and a second one read, so
+the flush's own dirty lines are written back before the step), and each step is bracketed
 by CUDA events on the solver's stream.  The JSON line reports MLUPS
 (node updates per second / 1e6), the roofline of the step kernel against the
 measured HBM bandwidth, an end-to-end number through the C ABI with host
@@ -46,6 +47,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=list(BYTES_PER_VALUE))
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default="auto", help="step-kernel variant (library default: auto)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="time every kernel variant and storage type; print one JSON line each")
     return ap.parse_args()
 
 
@@ -212,10 +216,39 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def make_solver(pkg, n, mesh, Ra, precision):
+def make_solver(pkg, n, mesh, Ra, precision, kernel="auto"):
     """A solver built entirely by the library (its own mesh helpers)."""
     xi = pkg.islbm_mesh_uniform(n) if mesh == "uniform" else getattr(pkg, "islbm_mesh_" + mesh)(n, 1.5)
-    return pkg.Solver(xi, xi, Ra=Ra, precision=precision)
+    return pkg.Solver(xi, xi, Ra=Ra, precision=precision, kernel=kernel)
+
+
+def sweep(args, pkg, torch, flush):
+    """Every step-kernel variant x storage type on the stretched mesh (and the
+    direct kernel on the uniform mesh), at n and at 4096^2."""
+    for n in (args.n, 4096):
+        for mesh in ("tanh", "uniform"):
+            for prec in ("fp32", "fp16dev", "bf16dev"):
+                kernels = ["direct"] if mesh == "uniform" else list(pkg.KERNELS)[1:]
+                for kern in kernels:
+                    s = make_solver(pkg, n, mesh, args.Ra, prec, kern)
+                    steps = min(args.steps, 400 if n <= 2048 else 100)
+                    t = timed_steps(pkg, s, steps, 5, flush, torch)
+                    nodes = n * n
+                    r = s.reduce(check=False)
+                    print(json.dumps({"sweep": True, "n": n, "mesh": mesh, "precision": prec,
+                                      "kernel": kern, "MLUPS": nodes * steps / (t * 1e6),
+                                      "GBps": 2 * 14 * BYTES_PER_VALUE[prec] * nodes / (t / steps) / 1e9,
+                                      "us_per_step": 1e6 * t / steps, "status": r["status"]}),
+                          flush=True)
+                    s.close()
+
+
+def flush_l2(flush):
+    """Write a 256 MB buffer (evicts everything the previous step left in the
+    126 MB L2), then read a second 256 MB buffer, so the write-backs of the
+    flush itself happen here and the timed step starts on a cold, clean L2."""
+    flush[0].zero_()
+    flush[1].sum()
 
 
 def timed_steps(pkg, solver, steps, warmup, flush, torch):
@@ -224,13 +257,13 @@ def timed_steps(pkg, solver, steps, warmup, flush, torch):
     solver.set_fields(temperature_noise(solver.shape, 1e-6, seed=0))
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
-        flush.zero_()
+        flush_l2(flush)
         solver.step(1)
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     for k in range(steps):
-        flush.zero_()
+        flush_l2(flush)
         starts[k].record(stream)
         solver.step(1)
         ends[k].record(stream)
@@ -259,8 +292,12 @@ def main():
 
     n = args.n
     nodes = n * n
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    solver = make_solver(pkg, n, args.mesh, args.Ra, args.precision)
+    flush = [torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda"),
+             torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")]
+    if args.sweep:
+        sweep(args, pkg, torch, flush)
+        return
+    solver = make_solver(pkg, n, args.mesh, args.Ra, args.precision, args.kernel)
     info = solver.info
 
     clocks = ClockSampler(local)
@@ -324,7 +361,7 @@ def main():
                        f"2-D cavity {n}x{n} {args.mesh}, Ra={args.Ra:g}",
                        "n": n, "mesh": args.mesh, "a": 1.5, "Ra": args.Ra, "Pr": 0.71,
                        "precision": args.precision, "parallelism": f"replicas{world}",
-                       "l2": "flushed before every timed step (256 MB write)",
+                       "l2": "before every timed step: 256 MB write, then 256 MB read of another buffer (cold, clean L2)",
                        "L_lu": info.L, "steps_per_tf": info.steps_per_tf},
             "wctpdt_s": ms_per_step * 1e-3 * info.steps_per_tf,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

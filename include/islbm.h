@@ -86,7 +86,13 @@ typedef struct {
   double s_e, s_eps, s_q, s_pi, s_m;   /* flow MRT rates (Sec. 2.1)            */
   double q_j, q_e, q_nu;               /* temperature MRT rates (Sec. 2.1)     */
   int stencil;        /* islbm_stencil                                          */
-  int reserved[7];
+  int kernel;         /* step-kernel variant of the 2-D FP32/16-bit path: 0 = chosen
+                         by the library; 1 direct (one thread per node); 2 tiled
+                         (cp.async tile staging); 3-6 persistent TMA pipelines
+                         (64x16 / 64x8 tiles, 2 / 3 stages: 3 = 16 rows 2 stages,
+                         4 = 8 rows 2 stages, 5 = 8 rows 3 stages, 6 = 16 rows
+                         3 stages).  Ignored for FP64, 3-D and the upwind stencil. */
+  int reserved[6];
 } islbm_params;
 
 /* Derived lattice-unit parameters of a handle. */
@@ -104,6 +110,8 @@ typedef struct {
   double steps_per_tf;   /* time steps per free-fall time, L/u_f (Sec. 3)       */
   double bytes_per_update; /* algorithmic HBM bytes of one node update          */
   long long time;     /* steps taken since the last set_* call                  */
+  int kernel;         /* step-kernel variant in use (see islbm_params.kernel)    */
+  int sm_count;       /* streaming multiprocessors of the device                */
 } islbm_info_t;
 
 /* Reductions of the current state (Sec. 3 and Sec. 4), accumulated in FP64. */

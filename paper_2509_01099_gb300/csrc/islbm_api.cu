@@ -111,6 +111,53 @@ unsigned long long fnv(const void* data, size_t n, unsigned long long h) {
   return h;
 }
 
+// TMA descriptors of the two population buffers for the pipelined 2-D kernels:
+// a 3-D tensor (x over the padded pitch, y, population plane) with a box of
+// one staged tile (64 + 2 halo chunks wide, 4R + 2 rows, all 14 planes).
+std::string encode_tensor_maps(Solver* s) {
+  typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                               const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                               const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return "cuTensorMapEncodeTiled is not available";
+  const int R = (s->variant == KV_TMA_R2S2 || s->variant == KV_TMA_R2S3) ? 2 : 4;
+  const int hx = 16 / (int)s->elem;
+  const CUtensorMapDataType dt = s->precision == ISLBM_FP32
+                                     ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                     : (s->precision == ISLBM_FP16DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  const cuuint64_t dims[3] = {(cuuint64_t)s->pitch, (cuuint64_t)s->n[1], 14};
+  const cuuint64_t strides[2] = {(cuuint64_t)s->pitch * s->elem, (cuuint64_t)s->plane * s->elem};
+  const cuuint32_t box[3] = {(cuuint32_t)(64 + 2 * hx), (cuuint32_t)(4 * R + 2), 14};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (int b = 0; b < 2; ++b) {
+    CUresult r = reinterpret_cast<EncodeFn>(fn)(
+        reinterpret_cast<CUtensorMap*>(s->tmap[b]), dt, 3, s->buf[b], dims, strides, box, estr,
+        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+  }
+  return "";
+}
+
+// Report (and clear) a timeout recorded by a pipelined kernel.  Synchronises.
+islbm_status check_device_flag(Solver* s) {
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, s->derr, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "reading the device error flag");
+  if (flag) {
+    cudaMemsetAsync(s->derr, 0, sizeof(int), s->stream);
+    return fail(s, ISLBM_ERR_TIMEOUT, "a bounded wait in the step kernel gave up");
+  }
+  return ISLBM_OK;
+}
+
 islbm_status finish_reductions(Solver* s, islbm_reductions* out) {
   const double* r = s->hresult;
   const Physics& h = s->ph;
@@ -223,6 +270,8 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
   if (!(prm.Ma > 0)) return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: Ma must be positive");
   if (prm.stencil != ISLBM_STENCIL_CENTRED && prm.stencil != ISLBM_STENCIL_UPWIND)
     return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: unknown stencil");
+  if (prm.kernel < 0 || prm.kernel >= KV_COUNT)
+    return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: unknown kernel variant");
   const double* xis[3] = {xi_x, xi_y, xi_z};
   const int ns[3] = {nx, ny, dim == 3 ? nz : 1};
   const char* names[3] = {"xi_x", "xi_y", "xi_z"};
@@ -321,6 +370,17 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
     return fail(nullptr, ISLBM_ERR_CUDA, "islbm_create: no CUDA device");
   }
   cudaGetDevice(&s->device);
+  cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+  // step-kernel variant: the pipelined TMA kernel for stretched 2-D meshes in
+  // FP32 / 16-bit storage, the direct kernel otherwise
+  if (prm.kernel != KV_AUTO)
+    s->variant = prm.kernel;
+  else
+    s->variant = (dim == 2 && precision != ISLBM_FP64 && !s->uniform)
+                     ? (precision == ISLBM_FP32 ? KV_TMA_R2S2 : KV_TMA_R4S2)
+                     : KV_DIRECT;
+  if (dim == 3 || precision == ISLBM_FP64 || prm.stencil != ISLBM_STENCIL_CENTRED)
+    s->variant = KV_DIRECT;
   s->elem = precision == ISLBM_FP64 ? 8 : (precision == ISLBM_FP32 ? 4 : 2);
   s->pitch = (s->n[0] + 31) / 32 * 32;
   s->plane = (long long)s->pitch * s->n[1] * s->n[2];
@@ -353,6 +413,14 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
   if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: reduction result");
   e = cudaMallocHost(&s->hresult, RED_STRIDE * sizeof(double));
   if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: pinned result");
+  e = cudaMalloc(&s->derr, sizeof(int));
+  if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: error flag");
+  e = cudaMemsetAsync(s->derr, 0, sizeof(int), s->stream);
+  if (e != cudaSuccess) return cleanup(ISLBM_ERR_CUDA, "islbm_create: error flag");
+  if (s->variant >= KV_TMA_R4S2) {
+    const std::string m = encode_tensor_maps(s);
+    if (!m.empty()) return cleanup(ISLBM_ERR_CUDA, "islbm_create: " + m);
+  }
   // pack the tables on the host and copy once
   std::vector<char> host(tab_bytes, 0);
   size_t off = 0;
@@ -432,6 +500,7 @@ extern "C" void islbm_destroy(islbm_t s) {
   if (s->dscratch) cudaFree(s->dscratch);
   if (s->dresult) cudaFree(s->dresult);
   if (s->dfield) cudaFree(s->dfield);
+  if (s->derr) cudaFree(s->derr);
   if (s->hresult) cudaFreeHost(s->hresult);
   delete s;
 }
@@ -461,6 +530,8 @@ extern "C" islbm_status islbm_info(islbm_t s, islbm_info_t* o) {
   o->steps_per_tf = h.L / h.u_f;
   o->bytes_per_update = 2.0 * (s->qf + s->qg) * (double)s->elem;
   o->time = s->time;
+  o->kernel = s->variant;
+  o->sm_count = s->sm_count;
   return ISLBM_OK;
 }
 
@@ -576,6 +647,10 @@ extern "C" islbm_status islbm_get_populations(islbm_t s, double* f, double* g) {
 
 extern "C" islbm_status islbm_reduce(islbm_t s, islbm_reductions* out) {
   if (!s || !out) return fail(s, ISLBM_ERR_ARG, "islbm_reduce: NULL argument");
+  {
+    const islbm_status st = check_device_flag(s);
+    if (st != ISLBM_OK) return st;
+  }
   CK(s, launch_reduce(*s));
   CK(s, cudaMemcpyAsync(s->hresult, s->dresult, RED_STRIDE * sizeof(double),
                         cudaMemcpyDeviceToHost, s->stream));
@@ -613,7 +688,7 @@ extern "C" islbm_status islbm_mass(islbm_t s, double* m) {
 extern "C" islbm_status islbm_synchronize(islbm_t s) {
   if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_synchronize: NULL handle");
   CK(s, cudaStreamSynchronize(s->stream));
-  return ISLBM_OK;
+  return check_device_flag(s);
 }
 
 // ============================================================================

@@ -11,6 +11,7 @@
 // wall rules (Sec. 2.3), forms the macroscopic moments and collides (Sec. 2.1),
 // which is the paper's collide -> stream -> interpolate cycle with the state
 // stored after the collision instead of before it.
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -470,37 +471,17 @@ struct TileGeom {
   }
 };
 
+// Compute phase of one staged tile: interpolated pull / walls -> collision ->
+// store.  `sm` holds the 14 staged planes (rows ry0.., columns x0-HX..);
+// `wyp` / `wym` are the packed y tables of the tile's first row (generic
+// pointers: shared or global memory).
 template <typename S, int R, bool UNI>
-__global__ void __launch_bounds__(kThreads, 2)
-    k_step_tiled(const S* __restrict__ fin, S* __restrict__ fout, P2<float> p) {
+__device__ __forceinline__ void tile_body(const S* __restrict__ sm, const float4* wyp,
+                                          const float4* wym, int x0, int y0, int ry0,
+                                          S* __restrict__ fout, const P2<float>& p) {
   using G = TileGeom<S, R>;
-  constexpr int TY = G::TY, HX = G::HX, SW = G::SW, SH = G::SH, CPR = G::CPR;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* sm = reinterpret_cast<S*>(smem_raw);
-  float4* wyt = reinterpret_cast<float4*>(smem_raw + (size_t)14 * G::PLANE * sizeof(S));
-
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
+  constexpr int TY = G::TY, HX = G::HX, SW = G::SW;
   const int cx0 = x0 - HX;
-  const int ry0 = max(0, min(y0 - 1, p.ny - 3));
-  // ---- stage the tile + halo of every plane ----
-  constexpr int CPP = SH * CPR;
-  for (int k = threadIdx.x; k < 14 * CPP; k += kThreads) {
-    const int pl = k / CPP;
-    const int r = k - pl * CPP;
-    const int row = r / CPR;
-    const int ch = r - row * CPR;
-    const int gy = ry0 + row, gx = cx0 + ch * HX;
-    const bool ok = gy < p.ny && gx >= 0 && gx + HX <= p.pitch;
-    const S* src = ok ? fin + (size_t)pl * p.plane + (size_t)gy * p.pitch + gx : fin;
-    cp_async16(sm + (size_t)pl * G::PLANE + row * SW + ch * HX, src, ok);
-  }
-  if (!UNI && threadIdx.x < 2 * TY) {
-    const int k = threadIdx.x / TY, yy = y0 + threadIdx.x % TY;
-    wyt[threadIdx.x] = yy < p.ny ? __ldg(p.py[k] + yy) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-
   const int c = threadIdx.x % kTX, rg = threadIdx.x / kTX;
   const int x = x0 + c;
   if (x >= p.nx) return;
@@ -552,7 +533,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (UNI) {
           out[m] = h[m + 1 - cy];
         } else {
-          const float4 q = wyt[(cy > 0 ? 0 : TY) + rg * R + m];
+          const float4 q = (cy > 0 ? wyp : wym)[rg * R + m];
           out[m] = q.x * h[m] + q.y * h[m + 1] + q.z * h[m + 2];
         }
       }
@@ -586,9 +567,14 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int lr = y - ry0;
       if (y >= p.ny) break;
       const bool wS = (y == 0), wN = (y == p.ny - 1);
-      const float4 qp = wyt[rg * R + m], qm = wyt[TY + rg * R + m];
-      const int brp = UNI ? lr - 1 : __float_as_int(qp.w) - ry0;
-      const int brm = UNI ? lr + 1 - 2 : __float_as_int(qm.w) - ry0;
+      float4 qp = make_float4(0.f, 0.f, 0.f, 0.f), qm = qp;
+      int brp = 0, brm = 0;
+      if (!UNI) {
+        qp = wyp[rg * R + m];
+        qm = wym[rg * R + m];
+        brp = __float_as_int(qp.w) - ry0;
+        brm = __float_as_int(qm.w) - ry0;
+      }
       auto ypull = [&](int pl, int cx, int cy) -> float {
         if (UNI) return (cx == 0) ? rd(pl, lr - cy, col) : xi(pl, lr - cy, cx);
         const float4 q = cy > 0 ? qp : qm;
@@ -634,6 +620,160 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 template <typename S, int R, bool UNI>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_step_tiled(const S* __restrict__ fin, S* __restrict__ fout, P2<float> p) {
+  using G = TileGeom<S, R>;
+  constexpr int TY = G::TY, HX = G::HX, SW = G::SW, SH = G::SH, CPR = G::CPR;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  S* sm = reinterpret_cast<S*>(smem_raw);
+  float4* wyt = reinterpret_cast<float4*>(smem_raw + (size_t)14 * G::PLANE * sizeof(S));
+
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
+  const int cx0 = x0 - HX;
+  const int ry0 = max(0, min(y0 - 1, p.ny - 3));
+  // ---- stage the tile + halo of every plane ----
+  constexpr int CPP = SH * CPR;
+  for (int k = threadIdx.x; k < 14 * CPP; k += kThreads) {
+    const int pl = k / CPP;
+    const int r = k - pl * CPP;
+    const int row = r / CPR;
+    const int ch = r - row * CPR;
+    const int gy = ry0 + row, gx = cx0 + ch * HX;
+    const bool ok = gy < p.ny && gx >= 0 && gx + HX <= p.pitch;
+    const S* src = ok ? fin + (size_t)pl * p.plane + (size_t)gy * p.pitch + gx : fin;
+    cp_async16(sm + (size_t)pl * G::PLANE + row * SW + ch * HX, src, ok);
+  }
+  if (!UNI && threadIdx.x < 2 * TY) {
+    const int k = threadIdx.x / TY, yy = y0 + threadIdx.x % TY;
+    wyt[threadIdx.x] = yy < p.ny ? __ldg(p.py[k] + yy) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  tile_body<S, R, UNI>(sm, wyt, wyt + TY, x0, y0, ry0, fout, p);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent TMA-pipelined step.  One CTA per SM slot walks the tiles in
+// row-major order; a single thread issues, for each tile, one 3-D TMA copy
+// (box SW x SH x 14 planes, out-of-range parts zero-filled) into one of
+// STAGES shared-memory buffers, tracked by an mbarrier, so the copies of the
+// next tiles are in flight while the current tile is computed.  Every
+// mbarrier wait is bounded: on timeout the CTA records an error flag, drains
+// its outstanding copies (again bounded) and returns.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after 2^22 polls (well under a second).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned phase) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <typename S, int R, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_step_tma(const __grid_constant__ CUtensorMap tmap, S* __restrict__ fout, P2<float> p,
+               int* err) {
+  using G = TileGeom<S, R>;
+  constexpr int TY = G::TY, HX = G::HX;
+  constexpr unsigned BUF = (unsigned)(14 * G::PLANE * sizeof(S));
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)STAGES * BUF);
+  const int ntx = (p.nx + kTX - 1) / kTX, nty = (p.ny + TY - 1) / TY;
+  const int ntiles = ntx * nty;
+  auto tile_origin = [&](int t, int& x0, int& y0, int& ry0) {
+    const int ty = t / ntx;
+    x0 = (t - ty * ntx) * kTX;
+    y0 = ty * TY;
+    ry0 = max(0, min(y0 - 1, p.ny - 3));
+  };
+  auto issue = [&](int t, int st) {
+    int x0, y0, ry0;
+    tile_origin(t, x0, y0, ry0);
+    mbar_expect_tx(&bars[st], BUF);
+    tma_load_3d(smem_raw + (size_t)st * BUF, &tmap, x0 - HX, ry0, 0, &bars[st]);
+  };
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < STAGES; ++st) mbar_init(&bars[st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int st = 0; st < STAGES; ++st) {
+      const int t = blockIdx.x + st * gridDim.x;
+      if (t < ntiles) issue(t, st);
+    }
+  for (int k = 0;; ++k) {
+    const int t = blockIdx.x + k * gridDim.x;
+    if (t >= ntiles) break;
+    const int st = k % STAGES;
+    const unsigned phase = (unsigned)(k / STAGES) & 1u;
+    const bool ok = mbar_wait(&bars[st], phase);
+    if (__syncthreads_or(!ok)) {
+      // a copy did not arrive: flag it, drain what is still in flight, leave
+      if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        for (int j = 0; j < STAGES; ++j) {
+          const int kk = k + j;
+          if (blockIdx.x + kk * gridDim.x < ntiles)
+            mbar_wait(&bars[kk % STAGES], (unsigned)(kk / STAGES) & 1u);
+        }
+      }
+      return;
+    }
+    int x0, y0, ry0;
+    tile_origin(t, x0, y0, ry0);
+    const S* sm = reinterpret_cast<const S*>(smem_raw + (size_t)st * BUF);
+    tile_body<S, R, false>(sm, p.py[0] + y0, p.py[1] + y0, x0, y0, ry0, fout, p);
+    __syncthreads();   // every thread is done with buffer st
+    if (threadIdx.x == 0) {
+      const int tn = t + STAGES * gridDim.x;
+      if (tn < ntiles) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        issue(tn, st);
+      }
+    }
+  }
+}
+
+template <typename S, int R, bool UNI>
 cudaError_t launch_tiled(const Solver& s, const S* in, S* out, const P2<float>& p) {
   using G = TileGeom<S, R>;
   static bool configured = false;
@@ -646,6 +786,28 @@ cudaError_t launch_tiled(const Solver& s, const S* in, S* out, const P2<float>& 
   }
   const dim3 grid((s.n[0] + kTX - 1) / kTX, (s.n[1] + G::TY - 1) / G::TY);
   k_step_tiled<S, R, UNI><<<grid, kThreads, G::smem_bytes(), s.stream>>>(in, out, p);
+  return cudaGetLastError();
+}
+
+
+template <typename S, int R, int STAGES>
+cudaError_t launch_tma(const Solver& s, int cur, S* out, const P2<float>& p) {
+  using G = TileGeom<S, R>;
+  constexpr size_t smem = (size_t)STAGES * 14 * G::PLANE * sizeof(S) + 64;
+  static int blocks_per_sm = 0;
+  if (blocks_per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_step_tma<S, R, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_step_tma<S, R, STAGES>,
+                                                      kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+  }
+  const int ntiles = ((s.n[0] + kTX - 1) / kTX) * ((s.n[1] + G::TY - 1) / G::TY);
+  const int grid = std::min(ntiles, s.sm_count * blocks_per_sm);
+  k_step_tma<S, R, STAGES><<<grid, kThreads, smem, s.stream>>>(
+      *reinterpret_cast<const CUtensorMap*>(s.tmap[cur]), out, p, s.derr);
   return cudaGetLastError();
 }
 
@@ -672,10 +834,18 @@ struct StepFn {
     const S* in = static_cast<const S*>(s.buf[s.cur]);
     S* out = static_cast<S*>(s.buf[s.cur ^ 1]);
     if constexpr (!std::is_same<S, double>::value) {
-      // the tiled kernel covers the centred stencil (its halo is one node)
-      // (on the uniform mesh the direct pure-shift kernel is faster)
-      if (s.stencil == ISLBM_STENCIL_CENTRED && !s.uniform)
-        return launch_tiled<S, 4, false>(s, in, out, p);
+      // the tiled kernels cover the centred stencil (their halo is one node);
+      // on the uniform mesh the direct pure-shift kernel is the default
+      if (s.stencil == ISLBM_STENCIL_CENTRED) {
+        switch (s.variant) {
+          case KV_TILED: return launch_tiled<S, 4, false>(s, in, out, p);
+          case KV_TMA_R4S2: return launch_tma<S, 4, 2>(s, s.cur, out, p);
+          case KV_TMA_R2S2: return launch_tma<S, 2, 2>(s, s.cur, out, p);
+          case KV_TMA_R2S3: return launch_tma<S, 2, 3>(s, s.cur, out, p);
+          case KV_TMA_R4S3: return launch_tma<S, 4, 3>(s, s.cur, out, p);
+          default: break;
+        }
+      }
     }
     if (s.uniform)
       k_step<S, true><<<grid2(s), block2(), 0, s.stream>>>(in, out, p);

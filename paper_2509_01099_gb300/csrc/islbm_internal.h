@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 ISLBM library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -30,6 +31,18 @@ enum RedSlot {
 };
 
 constexpr int RED_STRIDE = 16;   // doubles per block partial (>= RED_COUNT)
+
+// Step-kernel variants of the 2-D FP32/16-bit path (islbm_params.kernel).
+enum KernelVariant {
+  KV_AUTO = 0,      // chosen by the library (islbm_create)
+  KV_DIRECT = 1,    // one thread per node, interpolation from global memory
+  KV_TILED = 2,     // cp.async staging of a 64 x 16 tile, one tile per CTA
+  KV_TMA_R4S2 = 3,  // persistent, TMA double buffer, 64 x 16 tiles
+  KV_TMA_R2S2 = 4,  // persistent, TMA double buffer, 64 x 8 tiles
+  KV_TMA_R2S3 = 5,  // persistent, TMA triple buffer, 64 x 8 tiles
+  KV_TMA_R4S3 = 6,  // persistent, TMA triple buffer, 64 x 16 tiles
+  KV_COUNT
+};
 
 // Per-axis tables, built once on the host in FP64.
 struct Axis {
@@ -85,6 +98,10 @@ struct Solver {
   double* dfield = nullptr;       // staging for field upload / download (5 * nodes)
   std::string err;
   unsigned long long fingerprint = 0;
+  int variant = KV_DIRECT;        // step kernel of the 2-D FP32/16-bit path
+  int sm_count = 0;
+  int* derr = nullptr;            // device error flag of the pipelined kernels
+  alignas(128) unsigned char tmap[2][128];   // TMA descriptors of buf[0] / buf[1]
 };
 
 // ---- kernel launchers (islbm_d2.cu / islbm_d3.cu) ----

@@ -18,6 +18,8 @@ from . import build as _build
 LATTICES = {"d2q9_d2q5": 0, "d3q19_d3q7": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16dev": 2, "bf16dev": 3}
 STENCILS = {"centred": 0, "upwind": 1}
+KERNELS = {"auto": 0, "direct": 1, "tiled": 2, "tma_r4s2": 3, "tma_r2s2": 4, "tma_r2s3": 5,
+           "tma_r4s3": 6}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_DIVERGED",
           5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_IO"}
 
@@ -43,7 +45,7 @@ class Params(ctypes.Structure):
                 ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
                 ("s_pi", ctypes.c_double), ("s_m", ctypes.c_double), ("q_j", ctypes.c_double),
                 ("q_e", ctypes.c_double), ("q_nu", ctypes.c_double), ("stencil", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("kernel", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class Info(ctypes.Structure):
@@ -53,7 +55,7 @@ class Info(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("gbeta", ctypes.c_double), ("s_nu", ctypes.c_double),
                 ("a_T", ctypes.c_double), ("omega", ctypes.c_double),
                 ("steps_per_tf", ctypes.c_double), ("bytes_per_update", ctypes.c_double),
-                ("time", ctypes.c_longlong)]
+                ("time", ctypes.c_longlong), ("kernel", ctypes.c_int), ("sm_count", ctypes.c_int)]
 
 
 class Reductions(ctypes.Structure):
@@ -315,7 +317,9 @@ class Solver:
         if overrides:
             params = params if params is not None else islbm_default_params()
             for k, v in overrides.items():
-                setattr(params, k, STENCILS[v] if k == "stencil" and isinstance(v, str) else v)
+                if isinstance(v, str):
+                    v = {"stencil": STENCILS, "kernel": KERNELS}[k][v]
+                setattr(params, k, v)
         self.h = islbm_create(xi_x, xi_y, xi_z, Ra, Pr, None, precision, params, stream)
         self.info = islbm_info(self.h)
         self.dim = self.info.dim

@@ -224,3 +224,57 @@ def test_step_counter_and_zero_steps():
     with pytest.raises(pkg.IslbmError):
         s.step(-1)
     s.close()
+
+
+VARIANTS = ["direct", "tiled", "tma_r4s2", "tma_r2s2", "tma_r2s3", "tma_r4s3"]
+
+
+@pytest.mark.parametrize("kernel", VARIANTS)
+@pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
+@pytest.mark.parametrize("mesh", ["erf45", "uniform37x29", "tanh64"])
+def test_every_kernel_variant_random_state(mesh, precision, kernel):
+    """Each step-kernel variant, on ragged and tile-aligned meshes, from a random
+    state: every population after 3 steps."""
+    xi_x, xi_y = MESHES[mesh]()
+    cav = O.Cavity(xi_x, xi_y, params=O.Params(Ra=1e6))
+    f, g = _random_state(9, 5, cav.shape, seed=13)
+    cav.init_populations(f, g)
+    cav.step(3)
+    fp_ref, gp_ref = cav.post_collision()
+    s = pkg.Solver(xi_x, xi_y, Ra=1e6, precision=precision, kernel=kernel)
+    assert s.info.kernel == pkg.KERNELS[kernel]
+    s.set_populations(f, g)
+    s.step(3)
+    s.synchronize()
+    fp, gp = s.populations()
+    s.close()
+    tol = {"fp32": 5e-6, "fp16dev": 5e-3, "bf16dev": 5e-2}[precision]
+    assert np.abs(fp - fp_ref).max() / np.abs(fp_ref).max() <= tol
+    assert np.abs(gp - gp_ref).max() / np.abs(gp_ref).max() <= tol
+
+
+@pytest.mark.parametrize("kernel", VARIANTS)
+def test_every_kernel_variant_cavity(kernel):
+    ref = oracle_run("tanh64", 1e6, 1000)
+    xi_x, xi_y = MESHES["tanh64"]()
+    s = pkg.Solver(xi_x, xi_y, Ra=1e6, precision="fp32", kernel=kernel)
+    s.set_fields(temperature_noise(s.shape, 1e-6, seed=0))
+    s.step(1000)
+    got = s.fields()
+    red = s.reduce()
+    s.close()
+    assert rel_field_error(got["T"], ref["T"]) <= 1e-5
+    assert rel_vector_error([got["u"], got["v"]], [ref["u"], ref["v"]]) <= 1e-5
+    assert abs(red["Nu"] / ref["red"]["Nu"] - 1) <= 1e-4
+
+
+def test_default_kernel_choice():
+    s = pkg.Solver(O.mesh_tanh(64, 1.5), O.mesh_tanh(64, 1.5), Ra=1e6, precision="fp32")
+    assert s.info.kernel >= 3          # pipelined TMA kernel on a stretched mesh
+    s.close()
+    s = pkg.Solver(O.mesh_uniform(64), O.mesh_uniform(64), Ra=1e6, precision="fp32")
+    assert s.info.kernel == 1
+    s.close()
+    s = pkg.Solver(O.mesh_tanh(64, 1.5), O.mesh_tanh(64, 1.5), Ra=1e6, precision="fp64")
+    assert s.info.kernel == 1
+    s.close()
