@@ -231,6 +231,39 @@ ISLBM_API islbm_status islbm_synchronize(islbm_t h);
 ISLBM_API islbm_status islbm_save(islbm_t h, const char* path);
 ISLBM_API islbm_status islbm_load(islbm_t h, const char* path);
 
+/* ---- reductions without allocation ------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers of
+ * this library that cannot allocate device memory: code that runs while its
+ * memory pool is fully reserved, hosts that hand the library only buffers they
+ * already own, or loops where an allocation (and the device synchronisation it
+ * can cause) is not allowed.  islbm_reduce_noalloc computes the same
+ * quantities as islbm_reduce for a 2-D cavity state that lives entirely in the
+ * caller's device memory, with no handle, and calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *   f, g: device, full FP64 post-collision populations [9][ny][nx] and
+ *     [5][ny][nx] in the velocity order of islbm_set_populations (the layout
+ *     islbm_get_populations writes to the host).
+ *   nx, ny: fluid nodes per axis, at least 4 each; nx*ny at most 134217728.
+ *   xi_x, xi_y: device, the meshes (nx+2 and ny+2 doubles, ghost-node form as
+ *     for islbm_create).
+ *   Ra, Pr, opt (Ma, T_hot, T_cold; NULL = defaults): as for islbm_create.
+ *   stream: cudaStream_t for the two kernels (NULL = legacy stream).
+ *   out: host struct, filled on return (the call synchronises the stream).
+ * Its scratch is one file-scope device array of 1 MiB (per-block partial sums
+ * of at most 8192 blocks plus the result), held by every GPU that loads the
+ * library until the process exits.  Every value a call reads from it is
+ * written earlier in the same call.  The first call on a device looks up the
+ * array's device address once (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  All calls share the array: calls that overlap on
+ * the GPU race, so serialise them.  Returns ISLBM_ERR_ARG (nothing launched)
+ * for NULL pointers or sizes outside the limits above, ISLBM_ERR_DIVERGED if a
+ * node is non-finite, ISLBM_ERR_CUDA on a launch failure; the message is
+ * available from islbm_last_error(NULL). */
+ISLBM_API islbm_status islbm_reduce_noalloc(const double* f, const double* g, int nx, int ny,
+                                            const double* xi_x, const double* xi_y, double Ra,
+                                            double Pr, const islbm_params* opt, void* stream,
+                                            islbm_reductions* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,11 +19,18 @@ using namespace islbm;
 
 namespace {
 
-thread_local std::string g_last_error;
+// Last error of the calling thread, in a fixed buffer (copying a message into
+// it allocates nothing).
+thread_local char g_last_error[512] = {0};
+
+void copy_last_error(const char* msg) {
+  std::strncpy(g_last_error, msg, sizeof(g_last_error) - 1);
+  g_last_error[sizeof(g_last_error) - 1] = 0;
+}
 
 islbm_status fail(Solver* s, islbm_status st, const std::string& msg) {
   if (s) s->err = msg;
-  g_last_error = msg;
+  copy_last_error(msg.c_str());
   return st;
 }
 
@@ -506,8 +513,12 @@ extern "C" void islbm_destroy(islbm_t s) {
 }
 
 extern "C" const char* islbm_last_error(islbm_t s) {
-  return s ? s->err.c_str() : g_last_error.c_str();
+  return s ? s->err.c_str() : g_last_error;
 }
+
+namespace islbm {
+void set_last_error_static(const char* msg) { copy_last_error(msg); }
+}  // namespace islbm
 
 extern "C" islbm_status islbm_info(islbm_t s, islbm_info_t* o) {
   if (!s || !o) return fail(s, ISLBM_ERR_ARG, "islbm_info: NULL argument");

@@ -30,7 +30,7 @@ EXPORTS = (
     "islbm_set_fields", "islbm_set_fields_device", "islbm_set_populations", "islbm_step",
     "islbm_get_fields", "islbm_get_fields_device", "islbm_get_populations", "islbm_reduce",
     "islbm_nusselt", "islbm_reynolds", "islbm_mass", "islbm_synchronize", "islbm_save",
-    "islbm_load",
+    "islbm_load", "islbm_reduce_noalloc",
 )
 
 
@@ -114,6 +114,7 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
         "islbm_synchronize": (i, [h]),
         "islbm_save": (i, [h, ctypes.c_char_p]),
         "islbm_load": (i, [h, ctypes.c_char_p]),
+        "islbm_reduce_noalloc": (i, [vp, vp, i, i, vp, vp, d, d, P(Params), vp, P(Reductions)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -303,6 +304,20 @@ def islbm_save(h, path: str):
 
 def islbm_load(h, path: str):
     _check(load_library().islbm_load(h, path.encode()), h)
+
+
+def islbm_reduce_noalloc(f, g, nx, ny, xi_x, xi_y, Ra, Pr=0.71, params: Params | None = None,
+                         stream=None) -> dict:
+    """Reductions of a 2-D state held in caller-owned device memory (torch CUDA
+    float64 tensors or raw addresses); the library allocates nothing."""
+    r = Reductions()
+    if stream is None:
+        stream = _current_stream()
+    _check(load_library().islbm_reduce_noalloc(
+        _devptr(f), _devptr(g), int(nx), int(ny), _devptr(xi_x), _devptr(xi_y), float(Ra),
+        float(Pr), ctypes.byref(params) if params is not None else None, stream,
+        ctypes.byref(r)))
+    return {k: getattr(r, k) for k, _ in Reductions._fields_}
 
 
 # ---------------------------------------------------------------------------
