@@ -368,7 +368,7 @@ def main():
                          "frac": achieved / peak, "peak_source": peak_src,
                          "traffic": profile_traffic(),
                          "bytes_per_update": bytes_per_update,
-                         "kernel": "k_step (fused stream+interpolate+walls+collide)"},
+                         "kernel": "k_step_tma<float,2,2> (fused pull+interpolate+walls+collide, TMA-pipelined)"},
             "e2e": {"value": e2e_value, "unit": "MLUPS",
                     "h2d_bytes_per_step": 3 * 8 * nodes, "d2h_bytes_per_step": 8 * 16,
                     "definition": f"per step: set_fields from pinned host T,u,v + {inner} time steps + reduce read back"},
