@@ -71,9 +71,10 @@ def profile_traffic():
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         vals = {}
         for line in text.splitlines():
-            if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_sha256")):
+            line = line.strip().lstrip("-").strip()
+            if line.startswith(("traffic_bytes_per_launch:", "source_sha256:")):
                 k, v = line.split(":", 1)
-                vals[k.strip().lstrip("- ")] = v.strip().strip("`")
+                vals[k.strip()] = v.split()[0].strip("`")
         if vals.get("source_sha256") == sha:
             return float(vals["traffic_bytes_per_launch"])
     except Exception:
