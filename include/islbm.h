@@ -23,9 +23,11 @@
  *     independent.
  *   - There is no CPU fallback: without a CUDA device islbm_create returns
  *     ISLBM_ERR_CUDA.
- *   - Temperatures are the dimensionless T* = (T - T0)/dT with T0 the mean of
- *     the wall temperatures (hot wall +1/2, cold wall -1/2).  Velocities are in
- *     lattice units (l.u. per time step); u* = u / u_f with u_f from
+ *   - Temperatures are given in the units of the wall temperatures
+ *     (islbm_params.T_hot = +1/2, T_cold = -1/2 by default, so dT = 1); the
+ *     paper's T* = (T - T0)/dT uses the reference T0 of islbm_params.reference
+ *     (default: the cold wall, so T* = T + 1/2 lies in [0, 1]).  Velocities
+ *     are in lattice units (l.u. per time step); u* = u / u_f with u_f from
  *     islbm_info.
  */
 #ifndef ISLBM_H
@@ -92,8 +94,15 @@ typedef struct {
                          (64x16 / 64x8 tiles, 2 / 3 stages: 3 = 16 rows 2 stages,
                          4 = 8 rows 2 stages, 5 = 8 rows 3 stages, 6 = 16 rows
                          3 stages).  Ignored for FP64, 3-D and the upwind stencil. */
-  int reserved[6];
+  int reference;      /* reference temperature T0 of the buoyancy force and of T*
+                         (Sec. 2.1): ISLBM_TREF_COLD = the cold wall (default;
+                         reproduces the asymmetric centre values of Table 3),
+                         ISLBM_TREF_MEAN = mean of the wall temperatures          */
+  int reserved[5];
 } islbm_params;
+
+/* Choices of the reference temperature T0 (islbm_params.reference). */
+enum { ISLBM_TREF_MEAN = 0, ISLBM_TREF_COLD = 1 };
 
 /* Derived lattice-unit parameters of a handle. */
 typedef struct {
@@ -120,8 +129,10 @@ typedef struct {
   double Nu_hot;      /* minus the wall average of dT/dx (starred units), hot wall, Eq. (17) */
   double Nu_cold;     /* the same on the cold wall, Eq. (17)                      */
   double Nu_middle;   /* line average of sqrt(Ra Pr) u T - dT/dx (starred units) at x = 1/2 (2-D; NaN in 3-D) */
-  double Re;          /* <Re> = sqrt(Ra/Pr) <|u*|>_V                             */
-  double Re_uv;       /* same with sqrt(u*^2 + v*^2) (the printed 3-D form)      */
+  double Re;          /* <Re> = sqrt(Ra/Pr) sqrt(<|u*|^2>_V): root-mean-square speed,
+                         the form that reproduces the Re of Table 2              */
+  double Re_uv;       /* same with u*^2 + v*^2 only (the printed 3-D components) */
+  double Re_mean;     /* sqrt(Ra/Pr) <|u*|>_V, the volume-averaged speed         */
   double mass;        /* sum rho W (l.u.^d)                                      */
   double ke;          /* 1/2 sum |u|^2 W                                         */
   double max_speed;   /* max |u| / u_f                                           */
@@ -187,8 +198,10 @@ ISLBM_API islbm_status islbm_set_fields_device(islbm_t h, const double* rho, con
 
 /* Initialise from full pre-collision populations: host arrays f[q_flow][z][y][x]
  * and g[q_temp][z][y][x] in FP64, in the velocity order of the paper's
- * lattices as listed in the library's documentation.  The library collides
- * them and stores the result.  Resets the step counter. */
+ * lattices as listed in the library's documentation.  The temperature
+ * populations carry T - T_s, T_s the mean of the wall temperatures (zero for
+ * the default walls).  The library collides them and stores the result.
+ * Resets the step counter. */
 ISLBM_API islbm_status islbm_set_populations(islbm_t h, const double* f, const double* g);
 
 /* Advance n >= 0 ISLBM time steps (Sec. 2.2): virtual streaming with
@@ -215,6 +228,22 @@ ISLBM_API islbm_status islbm_get_populations(islbm_t h, double* f, double* g);
  * weighted with the midpoint rule of Eq. (18).  Synchronises.  Returns
  * ISLBM_ERR_DIVERGED (with *out filled) if any node is non-finite. */
 ISLBM_API islbm_status islbm_reduce(islbm_t h, islbm_reductions* out);
+
+/* Steady-state criterion of Sec. 3: *du = sum_i |u(t) - u(t')|_2 / sum_i |u(t')|_2
+ * and *dT = sum_i |T*(t) - T*(t')| / sum_i |T*(t')|, with t' the time of the
+ * previous call (the paper compares states 2000 steps apart).  The first call
+ * after creation or a set_* / load only records the state and returns +inf.
+ * Allocates a snapshot of (d+1) doubles per node on first use.  Synchronises. */
+ISLBM_API islbm_status islbm_steady_change(islbm_t h, double* du, double* dT);
+
+/* Advance in blocks of `interval` steps until both steady-state changes of
+ * islbm_steady_change fall below `tol` (the paper uses 1e-9 with interval 2000,
+ * Sec. 3), or `max_steps` have been taken (then ISLBM_ERR_NOT_CONVERGED).
+ * steps_done / du / dT (host, may be NULL) receive the steps taken and the last
+ * changes.  Synchronises after every block. */
+ISLBM_API islbm_status islbm_run_to_steady(islbm_t h, double tol, long long interval,
+                                           long long max_steps, long long* steps_done,
+                                           double* du, double* dT);
 
 /* Convenience views of islbm_reduce. */
 typedef struct { double vol, hot, cold, middle; } islbm_nu;

@@ -44,14 +44,23 @@ parameter below; the defaults are the readings):
       mesh already has this form; the uniform mesh of Eq. (14) is written with
       ghost nodes at -1/(2N) and 1 + 1/(2N)).  Walls lie 0.5 l.u. from the
       first and last fluid node; L = X_N - X_1 + 1 (Table 1).
-  R7  T0 is the mean of the wall temperatures: internally T_hot = +1/2,
-      T_cold = -1/2, T0 = 0 (reported T* = T + 1/2 lies in [0, 1]).
+  R7  T0, the reference temperature of the buoyancy force and of T* = (T-T0)/dT,
+      is the cold wall, while the temperature populations carry T - T_s with
+      T_s the mean wall temperature (walls at +1/2 and -1/2; T* = T + 1/2 lies
+      in [0, 1]).  The paper's tables fix both: Table 3's centre values
+      T_c = 0.49945 and u_c = -1.2163e-4 are not those of a centro-symmetric
+      field (which a mean-wall force reference gives), and Table 2's <Nu> and
+      Nu_middle lie 0.26% below Nu_hot, the signature of a convective flux
+      u T* evaluated with an offset from the transported temperature (with the
+      transported temperature equal to T*, <Nu> = Nu_hot to 1e-4).
   R8  Gravity points along -y: the buoyancy force is +rho g beta (T - T0) y-hat,
       which turns the cell clockwise with the hot wall on the left.
   R9  Nu_middle for even N is evaluated on the face between the two centre
       columns; for odd N on the centre column with a central derivative.
-  R10 3-D <Re> uses the full |u| (the printed 2-component form is also
-      returned as Re_uv).
+  R10 <Re> uses the root-mean-square speed, sqrt(Ra/Pr) sqrt(<u*^2 + v*^2>_V):
+      it reproduces Table 2 (the printed <sqrt(u*^2 + v*^2)>_V, returned as
+      Re_mean, is ~27% lower than the tabulated values).  In 3-D |u| includes
+      w; the printed two-component form is returned as Re_uv.
 """
 from __future__ import annotations
 
@@ -392,7 +401,7 @@ class Params:
     Ma: float = 0.1
     T_hot: float = 0.5
     T_cold: float = -0.5
-    T0: float = 0.0
+    T0: float | None = None          # None: the cold wall (reading R7)
     s_rho: float = 1.0
     s_j: float = 1.0
     s_e: float | None = None
@@ -464,6 +473,8 @@ class Cavity:
 
     def __init__(self, xi_x, xi_y, xi_z=None, params: Params | None = None):
         self.p = params if params is not None else Params(Ra=1e6)
+        self.T0 = self.p.T_cold if self.p.T0 is None else self.p.T0
+        self.Ts = 0.5 * (self.p.T_hot + self.p.T_cold)
         meshes = [np.asarray(xi_x, float), np.asarray(xi_y, float)]
         if xi_z is not None:
             meshes.append(np.asarray(xi_z, float))
@@ -493,10 +504,10 @@ class Cavity:
         return vec.reshape(shape)
 
     # ---- equilibria and macroscopic quantities (Sec. 2.1) -----------------
-    def equilibrium(self, rho, u, T):
-        """f^eq = M^-1 m^eq(rho, u) and g^eq = N^-1 n^eq(T, u)."""
+    def equilibrium(self, rho, u, theta):
+        """f^eq = M^-1 m^eq(rho, u) and g^eq = N^-1 n^eq(theta, u), theta = T - T_s (R7)."""
         meq = np.array(self.flow.meq(rho, u))
-        neq = np.array(self.thermal.neq(T, u, self.par.a_T))
+        neq = np.array(self.thermal.neq(theta, u, self.par.a_T))
         f = np.tensordot(self.flow.Minv, meq, axes=1)
         g = np.tensordot(self.thermal.Ninv, neq, axes=1)
         return f, g
@@ -508,30 +519,32 @@ class Cavity:
             u = [np.zeros(self.shape) for _ in range(self.d)]
         if rho is None:
             rho = np.ones(self.shape)
-        self.f, self.g = self.equilibrium(rho, [np.asarray(c, float).reshape(self.shape) for c in u], T)
+        self.f, self.g = self.equilibrium(rho, [np.asarray(c, float).reshape(self.shape) for c in u],
+                                          T - self.Ts)
         self.time = 0
 
     def init_populations(self, f, g):
+        """Pre-collision populations; the temperature populations carry T - T_s (R7)."""
         self.f = np.array(f, dtype=np.float64).reshape((self.flow.q,) + self.shape)
         self.g = np.array(g, dtype=np.float64).reshape((self.thermal.q,) + self.shape)
         self.time = 0
 
     def macroscopic(self, f, g):
-        """rho = sum f, T = sum g, F = rho g beta (T - T0) y-hat (R8),
-        u = (sum e f + F/2)/rho (Sec. 2.1)."""
+        """rho = sum f, theta = T - T_s = sum g, F = rho g beta (T - T0) y-hat (R7, R8),
+        u = (sum e f + F/2)/rho (Sec. 2.1).  Returns rho, u, theta, F."""
         rho = f.sum(axis=0)
-        T = g.sum(axis=0)
+        theta = g.sum(axis=0)
         F = [np.zeros(self.shape) for _ in range(self.d)]
-        F[1] = rho * self.par.gbeta * (T - self.p.T0)
+        F[1] = rho * self.par.gbeta * (theta + self.Ts - self.T0)
         u = [(np.tensordot(self.flow.e[:, a].astype(float), f, axes=1) + 0.5 * F[a]) / rho
              for a in range(self.d)]
-        return rho, u, T, F
+        return rho, u, theta, F
 
     # ---- collision (Sec. 2.1, collision steps) ----------------------------
     def collide(self, f, g):
         """f+ = f - M^-1 S (m - m^eq) + F',  F' = M^-1 (I - S/2) M F~;
         g+ = g - N^-1 Q (n - n^eq)."""
-        rho, u, T, F = self.macroscopic(f, g)
+        rho, u, theta, F = self.macroscopic(f, g)
         M, Minv, S = self.flow.M, self.flow.Minv, self.par.S
         m = np.tensordot(M, f, axes=1)
         meq = np.array(self.flow.meq(rho, u))
@@ -541,7 +554,7 @@ class Cavity:
             + np.tensordot(Minv, (1.0 - relax / 2.0) * MF, axes=1)
         Nm, Ninv, Q = self.thermal.N, self.thermal.Ninv, self.par.Q
         n = np.tensordot(Nm, g, axes=1)
-        neq = np.array(self.thermal.neq(T, u, self.par.a_T))
+        neq = np.array(self.thermal.neq(theta, u, self.par.a_T))
         qrel = Q.reshape((-1,) + (1,) * self.d)
         gpost = g - np.tensordot(Ninv, qrel * (n - neq), axes=1)
         return fpost, gpost
@@ -568,7 +581,7 @@ class Cavity:
     def stream(self, fpost, gpost):
         """f_i(x, t+dt) from the interpolated virtual streaming, or half-way
         bounce-back f_i = f_ibar+ where the departure point lies behind a wall.
-        g: anti-bounce-back g_i = -g_ibar+ + omega T_w on the isothermal x-walls,
+        g: anti-bounce-back g_i = -g_ibar+ + omega (T_w - T_s) on the isothermal x-walls,
         bounce-back g_i = g_ibar+ on the adiabatic walls (Sec. 2.3)."""
         fl, th = self.flow, self.thermal
         fnew = np.empty_like(fpost)
@@ -583,7 +596,7 @@ class Cavity:
             mask = self._wall_mask(e_i)
             if e_i[0] != 0:       # x-directed: isothermal walls
                 T_w = self.p.T_hot if e_i[0] == +1 else self.p.T_cold
-                wallval = -gpost[th.opp[i]] + self.par.omega * (T_w - self.p.T0)
+                wallval = -gpost[th.opp[i]] + self.par.omega * (T_w - self.Ts)
             else:                 # y- or z-directed: adiabatic walls
                 wallval = gpost[th.opp[i]]
             gnew[i] = np.where(mask, wallval, val)
@@ -598,9 +611,9 @@ class Cavity:
 
     # ---- diagnostics (Sec. 2.3, Sec. 3, Sec. 4) ---------------------------
     def fields(self):
-        """rho, u (list per axis), T at the current time (internal T convention)."""
-        rho, u, T, _ = self.macroscopic(self.f, self.g)
-        return rho, u, T
+        """rho, u (list per axis), T at the current time (in the units of T_hot, T_cold)."""
+        rho, u, theta, _ = self.macroscopic(self.f, self.g)
+        return rho, u, theta + self.Ts
 
     def post_collision(self):
         return self.collide(self.f, self.g)
@@ -624,7 +637,7 @@ class Cavity:
         return (4 * q * (q + 1) * Tw - (2 * q + 1) ** 2 * T1 + T2) / (q * (2 * q + 1))
 
     def reductions(self):
-        """<Nu>, Nu_hot, Nu_cold, Nu_middle (2-D), <Re>, mass, kinetic energy (Sec. 3, Sec. 4).
+        """<Nu>, Nu_hot, Nu_cold, Nu_middle (2-D), <Re> (R10), mass, kinetic energy (Sec. 3, Sec. 4).
 
         <phi>_V = sum phi prod W / sum prod W (Eq. (18) on every axis, divided by
         the cavity volume, L^d for the square cavity); u* = u/u_f,
@@ -633,17 +646,17 @@ class Cavity:
         rho, u, T = self.fields()
         par, p, L, d = self.par, self.p, self.L, self.d
         dT = p.T_hot - p.T_cold
-        Ts = (T - p.T0) / dT
+        Ts = (T - self.T0) / dT
         us = [c / par.u_f for c in u]
         Wv = self.volume_weights()
         vol = float(Wv.sum())           # L^d for the square / cubic cavity
         out = {}
         out["Nu"] = math.sqrt(p.Ra * p.Pr) * float((Wv * us[0] * Ts).sum()) / vol + 1.0
-        speed = np.sqrt(sum(c * c for c in us))
-        out["Re"] = math.sqrt(p.Ra / p.Pr) * float((Wv * speed).sum()) / vol
-        if d == 3:
-            out["Re_uv"] = math.sqrt(p.Ra / p.Pr) * float(
-                (Wv * np.sqrt(us[0] ** 2 + us[1] ** 2)).sum()) / vol
+        speed2 = sum(c * c for c in us)
+        out["Re"] = math.sqrt(p.Ra / p.Pr) * math.sqrt(float((Wv * speed2).sum()) / vol)
+        out["Re_mean"] = math.sqrt(p.Ra / p.Pr) * float((Wv * np.sqrt(speed2)).sum()) / vol
+        out["Re_uv"] = math.sqrt(p.Ra / p.Pr) * math.sqrt(
+            float((Wv * (us[0] ** 2 + us[1] ** 2)).sum()) / vol)
         out["mass"] = float((Wv * rho).sum())
         out["ke"] = float((Wv * sum(c * c for c in u)).sum()) * 0.5
         # wall-plane weights: every axis but x

@@ -7,8 +7,8 @@ from .islbm import (EXPORTS, KERNELS, LATTICES, PRECISIONS, STENCILS, IslbmError
                     islbm_create, islbm_default_params, islbm_destroy, islbm_get_fields,
                     islbm_get_fields_device, islbm_get_populations, islbm_info, islbm_load,
                     islbm_mass, islbm_mesh_erf, islbm_mesh_tanh, islbm_mesh_uniform,
-                    islbm_nusselt, islbm_reduce, islbm_reduce_noalloc, islbm_reynolds, islbm_save, islbm_set_fields,
-                    islbm_set_fields_device, islbm_set_populations, islbm_step,
+                    islbm_nusselt, islbm_reduce, islbm_reduce_noalloc, islbm_reynolds, islbm_run_to_steady, islbm_save, islbm_set_fields,
+                    islbm_set_fields_device, islbm_set_populations, islbm_steady_change, islbm_step,
                     islbm_synchronize, library_path, load_library)
 
 __all__ = [n for n in dir() if not n.startswith("_")]

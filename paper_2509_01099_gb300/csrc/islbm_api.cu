@@ -181,10 +181,14 @@ islbm_status finish_reductions(Solver* s, islbm_reductions* out) {
   const double dT = h.dT;
   islbm_reductions o;
   std::memset(&o, 0, sizeof(o));
-  // <Nu> = sqrt(Ra Pr) <u* T*>_V + 1, <Re> = sqrt(Ra/Pr) <|u*|>_V (Sec. 3, Sec. 4)
+  // <Nu> = sqrt(Ra Pr) <u* T*>_V + 1 (Sec. 3, Sec. 4); <Re> = sqrt(Ra/Pr) times
+  // the root-mean-square speed (the reading that reproduces Table 2), the
+  // volume-averaged speed as Re_mean, and the (u, v) root-mean-square as Re_uv
+  const double sra = std::sqrt(h.Ra / h.Pr);
   o.Nu = std::sqrt(h.Ra * h.Pr) * r[RED_UT] / (h.u_f * dT * vol) + 1.0;
-  o.Re = std::sqrt(h.Ra / h.Pr) * r[RED_SPEED] / (h.u_f * vol);
-  o.Re_uv = std::sqrt(h.Ra / h.Pr) * r[RED_SPEED_UV] / (h.u_f * vol);
+  o.Re = sra * std::sqrt(r[RED_U2] / vol) / h.u_f;
+  o.Re_uv = sra * std::sqrt(r[RED_UV2] / vol) / h.u_f;
+  o.Re_mean = sra * r[RED_SPEED] / (h.u_f * vol);
   o.mass = r[RED_MASS];
   o.ke = 0.5 * r[RED_U2];
   // Nu_hot / Nu_cold = -<dT*/dx*> with dT*/dx* = (L/dT) dT/dX by Eq. (17); the
@@ -250,6 +254,7 @@ extern "C" void islbm_default_params(islbm_params* p) {
   p->T_hot = 0.5;
   p->T_cold = -0.5;
   p->stencil = ISLBM_STENCIL_CENTRED;
+  p->reference = ISLBM_TREF_COLD;
 }
 
 // ============================================================================
@@ -321,7 +326,12 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
   h.gbeta = h.u_f * h.u_f / h.L;
   h.T_hot = prm.T_hot;
   h.T_cold = prm.T_cold;
-  h.T0 = 0.5 * (prm.T_hot + prm.T_cold);
+  if (prm.reference != ISLBM_TREF_MEAN && prm.reference != ISLBM_TREF_COLD) {
+    delete s;
+    return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: unknown reference temperature");
+  }
+  h.T0 = prm.reference == ISLBM_TREF_COLD ? prm.T_cold : 0.5 * (prm.T_hot + prm.T_cold);
+  h.Ts = 0.5 * (prm.T_hot + prm.T_cold);
   h.dT = (prm.T_hot != prm.T_cold) ? prm.T_hot - prm.T_cold : 1.0;
   h.s_nu = 1.0 / (3.0 * h.nu + 0.5);
   const double magic = 8.0 * (2.0 - h.s_nu) / (8.0 - h.s_nu);
@@ -508,6 +518,7 @@ extern "C" void islbm_destroy(islbm_t s) {
   if (s->dresult) cudaFree(s->dresult);
   if (s->dfield) cudaFree(s->dfield);
   if (s->derr) cudaFree(s->derr);
+  if (s->dsnap) cudaFree(s->dsnap);
   if (s->hresult) cudaFreeHost(s->hresult);
   delete s;
 }
@@ -567,6 +578,7 @@ extern "C" islbm_status islbm_set_fields_device(islbm_t s, const double* rho, co
   if (s->dim == 2 && w) return fail(s, ISLBM_ERR_ARG, "islbm_set_fields: w must be NULL in 2-D");
   CK(s, launch_init_fields(*s, rho, T, u, v, w));
   s->time = 0;
+  s->snap_valid = false;
   return ISLBM_OK;
 }
 
@@ -588,6 +600,7 @@ extern "C" islbm_status islbm_set_fields(islbm_t s, const double* rho, const dou
   CK(s, launch_init_fields(*s, dst[0], dst[1], dst[2], dst[3], dst[4]));
   CK(s, cudaStreamSynchronize(s->stream));
   s->time = 0;
+  s->snap_valid = false;
   return ISLBM_OK;
 }
 
@@ -603,6 +616,7 @@ extern "C" islbm_status islbm_set_populations(islbm_t s, const double* f, const 
   CK(s, launch_init_populations(*s, df, dg));
   CK(s, cudaStreamSynchronize(s->stream));
   s->time = 0;
+  s->snap_valid = false;
   return ISLBM_OK;
 }
 
@@ -667,6 +681,61 @@ extern "C" islbm_status islbm_reduce(islbm_t s, islbm_reductions* out) {
                         cudaMemcpyDeviceToHost, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
   return finish_reductions(s, out);
+}
+
+extern "C" islbm_status islbm_steady_change(islbm_t s, double* du, double* dT) {
+  if (!s || !du || !dT) return fail(s, ISLBM_ERR_ARG, "islbm_steady_change: NULL argument");
+  if (!s->dsnap) {
+    const size_t n = (size_t)(s->dim + 1) * (size_t)s->nodes * sizeof(double);
+    cudaError_t e = cudaMalloc(&s->dsnap, n);
+    if (e != cudaSuccess) return cuda_fail(s, e, "steady-state snapshot");
+    s->snap_valid = false;
+  }
+  {
+    const islbm_status st = check_device_flag(s);
+    if (st != ISLBM_OK) return st;
+  }
+  CK(s, launch_steady(*s));
+  CK(s, cudaMemcpyAsync(s->hresult, s->dresult, RED_STRIDE * sizeof(double),
+                        cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  const double* r = s->hresult;
+  if (!s->snap_valid) {
+    *du = *dT = INFINITY;
+  } else {
+    *du = r[1] > 0 ? r[0] / r[1] : (r[0] > 0 ? INFINITY : 0.0);
+    *dT = r[3] > 0 ? r[2] / r[3] : (r[2] > 0 ? INFINITY : 0.0);
+  }
+  s->snap_valid = true;
+  if (!std::isfinite(r[0]) || !std::isfinite(r[2]))
+    return fail(s, ISLBM_ERR_DIVERGED, "non-finite values in the state");
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_run_to_steady(islbm_t s, double tol, long long interval,
+                                            long long max_steps, long long* steps_done,
+                                            double* du_out, double* dT_out) {
+  if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_run_to_steady: NULL handle");
+  if (!(tol > 0) || interval <= 0 || max_steps < 0)
+    return fail(s, ISLBM_ERR_ARG, "islbm_run_to_steady: tol > 0, interval > 0, max_steps >= 0");
+  double du = INFINITY, dT = INFINITY;
+  long long done = 0;
+  islbm_status st = islbm_steady_change(s, &du, &dT);   // snapshot of the starting state
+  while (st == ISLBM_OK && done < max_steps) {
+    const long long n = std::min(interval, max_steps - done);
+    st = islbm_step(s, n);
+    if (st != ISLBM_OK) break;
+    done += n;
+    st = islbm_steady_change(s, &du, &dT);
+    if (st == ISLBM_OK && n == interval && du < tol && dT < tol) break;
+  }
+  if (steps_done) *steps_done = done;
+  if (du_out) *du_out = du;
+  if (dT_out) *dT_out = dT;
+  if (st != ISLBM_OK) return st;
+  if (!(du < tol && dT < tol))
+    return fail(s, ISLBM_ERR_NOT_CONVERGED, "islbm_run_to_steady: step budget exhausted");
+  return ISLBM_OK;
 }
 
 extern "C" islbm_status islbm_nusselt(islbm_t s, islbm_nu* out) {
@@ -755,5 +824,6 @@ extern "C" islbm_status islbm_load(islbm_t s, const char* path) {
   CK(s, cudaMemcpyAsync(s->buf[s->cur], host.data(), bytes, cudaMemcpyHostToDevice, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
   s->time = hd.time;
+  s->snap_valid = false;
   return ISLBM_OK;
 }

@@ -6,7 +6,8 @@
 //   D2Q9: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
 //   D2Q5: (0,0) (1,0) (0,1) (-1,0) (0,-1).
 // The stored state of time t is the post-collision deviation f_i^+ - w_i
-// (g_i^+ - t_i T0).  One step therefore pulls the post-collision values
+// (g_i^+, the temperature populations carrying T - T_s with T_s the mean wall
+// temperature).  One step therefore pulls the post-collision values
 // through the virtual streaming + quadratic interpolation (Sec. 2.2) or the
 // wall rules (Sec. 2.3), forms the macroscopic moments and collides (Sec. 2.1),
 // which is the paper's collide -> stream -> interpolate cycle with the state
@@ -31,8 +32,11 @@ struct P2 {
   const R* wy[2];
   const float4* px[2];  // packed FP32 tables of the tiled kernel
   const float4* py[2];
-  R gbeta, T0, s_e, s_eps, s_q, s_nu, q_j, q_e, q_nu, a_T;
-  R abb_hot, abb_cold;  // omega (T_w - T0) of the anti-bounce-back rule
+  // The temperature populations carry T - T_s (T_s: mean wall temperature);
+  // the buoyancy force is rho g beta (T - T_ref) = rho g beta (T - T_s + Fb).
+  R gbeta, s_e, s_eps, s_q, s_nu, q_j, q_e, q_nu, a_T;
+  R Ts, Fb;             // T_s and T_s - T_ref
+  R abb_hot, abb_cold;  // omega (T_w - T_s) of the anti-bounce-back rule
 };
 
 // Rest weights w_i of the D2Q9 populations.
@@ -46,7 +50,9 @@ __device__ __forceinline__ R wrest(int i) {
 //   m+ = m - S (m - m_eq) + (I - S/2) M F~ with the printed m_eq and M F~;
 //   f+ = f + M^-1 (m+ - m), M^-1 = M^T diag(1/|row_k|^2).
 //   g: n = N g with rows (T, jx, jy, -4+5|c|^2, cx^2-cy^2), n+ = n - Q (n - n_eq).
-// The buoyancy F = rho g beta (T - T0) acts along +y; u = (sum e f + F/2)/rho.
+// The buoyancy F = rho g beta (T - T_ref) acts along +y; u = (sum e f + F/2)/rho.
+// The populations carry T - T_s, which is also the temperature of the
+// equilibrium fluxes u T and of a_T T.
 // Returns rho, u and T of the pre-collision state.
 template <typename R>
 __device__ __forceinline__ void collide(R (&f)[9], R (&g)[5], const P2<R>& p, R& rho_o,
@@ -55,9 +61,9 @@ __device__ __forceinline__ void collide(R (&f)[9], R (&g)[5], const P2<R>& p, R&
   const R rho = R(1) + drho;
   const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
   const R jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-  const R Tr = (g[0] + g[1]) + (g[2] + g[3]) + g[4];  // T - T0
-  const R T = Tr + p.T0;
-  const R Fy = rho * p.gbeta * Tr;
+  const R Tr = (g[0] + g[1]) + (g[2] + g[3]) + g[4];  // T - T_s
+  const R T = Tr;
+  const R Fy = rho * p.gbeta * (Tr + p.Fb);
   const R inv = R(1) / rho;
   const R ux = jx * inv;
   const R uy = (jy + R(0.5) * Fy) * inv;
@@ -212,7 +218,7 @@ __global__ void k_init_fields(S* __restrict__ fout, P2<typename Store<S>::R> p,
   if (x >= p.nx || y >= p.ny) return;
   const size_t node = (size_t)y * p.nx + x;
   const R rho = rho_in ? R(rho_in[node]) : R(1);
-  const R T = R(T_in[node]);
+  const R T = R(T_in[node] - (double)p.Ts);   // T - T_s
   const R ux = u_in ? R(u_in[node]) : R(0);
   const R uy = v_in ? R(v_in[node]) : R(0);
   const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -225,7 +231,7 @@ __global__ void k_init_fields(S* __restrict__ fout, P2<typename Store<S>::R> p,
     f[i] = wrest<R>(i) * (rho * (R(1) + R(3) * eu + R(4.5) * eu * eu - R(1.5) * usq) - R(1));
   }
   const R t0 = (R(1) - p.a_T) * R(0.2), ti = (R(4) + p.a_T) * R(0.05);
-  const R Tr = T - p.T0;
+  const R Tr = T;
   g[0] = t0 * Tr;
 #pragma unroll
   for (int i = 1; i < 5; ++i) g[i] = ti * Tr + R(0.5) * (R(ex[i]) * ux + R(ey[i]) * uy) * T;
@@ -248,12 +254,11 @@ __global__ void k_init_pops(S* __restrict__ fout, P2<typename Store<S>::R> p,
   if (x >= p.nx || y >= p.ny) return;
   const size_t nodes = (size_t)p.nx * p.ny;
   const size_t node = (size_t)y * p.nx + x;
-  const R t0 = (R(1) - p.a_T) * R(0.2), ti = (R(4) + p.a_T) * R(0.05);
   R f[9], g[5];
 #pragma unroll
   for (int i = 0; i < 9; ++i) f[i] = R(fin[i * nodes + node] - wrest<double>(i));
 #pragma unroll
-  for (int i = 0; i < 5; ++i) g[i] = R(gin[i * nodes + node]) - (i == 0 ? t0 : ti) * p.T0;
+  for (int i = 0; i < 5; ++i) g[i] = R(gin[i * nodes + node]);
   R r_, a_, b_, c_;
   collide(f, g, p, r_, a_, b_, c_);
   const size_t idx = (size_t)y * p.pitch + x;
@@ -272,7 +277,8 @@ struct NodeState {
 
 template <typename S>
 __device__ __forceinline__ NodeState node_state(const S* __restrict__ s, size_t idx,
-                                                long long P, double gbeta, double T0) {
+                                                long long P, double gbeta, double Ts,
+                                                double Tref) {
   double f[9], g[5];
 #pragma unroll
   for (int i = 0; i < 9; ++i) f[i] = (double)Store<S>::ld(s + i * P + idx);
@@ -284,8 +290,8 @@ __device__ __forceinline__ NodeState node_state(const S* __restrict__ s, size_t 
   const double jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
   const double jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
   const double Tr = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
-  n.T = Tr + T0;
-  const double Fy = n.rho * gbeta * Tr;
+  n.T = Tr + Ts;
+  const double Fy = n.rho * gbeta * (n.T - Tref);
   n.ux = jx / n.rho;
   n.uy = (jy - 0.5 * Fy) / n.rho;
   return n;
@@ -293,11 +299,11 @@ __device__ __forceinline__ NodeState node_state(const S* __restrict__ s, size_t 
 
 template <typename S>
 __global__ void k_fields(const S* __restrict__ s, P2<typename Store<S>::R> p, double gbeta,
-                         double T0, double* rho, double* T, double* u, double* v) {
+                         double Ts, double Tref, double* rho, double* T, double* u, double* v) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
-  const NodeState n = node_state(s, (size_t)y * p.pitch + x, p.plane, gbeta, T0);
+  const NodeState n = node_state(s, (size_t)y * p.pitch + x, p.plane, gbeta, Ts, Tref);
   const size_t node = (size_t)y * p.nx + x;
   if (rho) rho[node] = n.rho;
   if (T) T[node] = n.T;
@@ -314,14 +320,11 @@ __global__ void k_pops(const S* __restrict__ s, P2<typename Store<S>::R> p, doub
   if (x >= p.nx || y >= p.ny) return;
   const size_t nodes = (size_t)p.nx * p.ny, node = (size_t)y * p.nx + x;
   const size_t idx = (size_t)y * p.pitch + x;
-  const double t0 = (1.0 - (double)p.a_T) * 0.2, ti = (4.0 + (double)p.a_T) * 0.05;
 #pragma unroll
   for (int i = 0; i < 9; ++i)
     f[i * nodes + node] = (double)Store<S>::ld(s + i * p.plane + idx) + wrest<double>(i);
 #pragma unroll
-  for (int i = 0; i < 5; ++i)
-    g[i * nodes + node] =
-        (double)Store<S>::ld(s + (9 + i) * p.plane + idx) + (i == 0 ? t0 : ti) * (double)p.T0;
+  for (int i = 0; i < 5; ++i) g[i * nodes + node] = (double)Store<S>::ld(s + (9 + i) * p.plane + idx);
 }
 
 // FP64 reductions of the current state (Sec. 3): every node adds its
@@ -330,7 +333,8 @@ __global__ void k_pops(const S* __restrict__ s, P2<typename Store<S>::R> p, doub
 // which the host finishes Eq. (17) and Nu_middle.
 template <typename S>
 __global__ void __launch_bounds__(256)
-    k_reduce(const S* __restrict__ s, P2<typename Store<S>::R> p, double gbeta, double T0,
+    k_reduce(const S* __restrict__ s, P2<typename Store<S>::R> p, double gbeta, double Ts,
+             double T0,
              const double* __restrict__ Wx, const double* __restrict__ Wy, double* partial) {
   double acc[RED_COUNT];
 #pragma unroll
@@ -342,7 +346,7 @@ __global__ void __launch_bounds__(256)
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nodes;
        k += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(k / p.nx), x = (int)(k - (long long)y * p.nx);
-    const NodeState n = node_state(s, (size_t)y * p.pitch + x, p.plane, gbeta, T0);
+    const NodeState n = node_state(s, (size_t)y * p.pitch + x, p.plane, gbeta, Ts, T0);
     const double W = Wx[x] * Wy[y];
     const double u2 = n.ux * n.ux + n.uy * n.uy;
     const double sp = sqrt(u2);
@@ -350,7 +354,7 @@ __global__ void __launch_bounds__(256)
     acc[RED_MASS] += W * n.rho;
     acc[RED_UT] += W * n.ux * Tr;
     acc[RED_SPEED] += W * sp;
-    acc[RED_SPEED_UV] += W * sp;
+    acc[RED_UV2] += W * u2;
     acc[RED_U2] += W * u2;
     const double wy = Wy[y];
     if (x == 0) acc[RED_HOT1] += wy * n.T;
@@ -379,6 +383,43 @@ __global__ void __launch_bounds__(256)
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
       v = (k == RED_MAXSPEED) ? fmax(v, sh[w][k]) : v + sh[w][k];
     partial[(size_t)blockIdx.x * RED_STRIDE + k] = v;
+  }
+}
+
+// Steady-state criterion (Sec. 3): sum |u(t) - u(t0)|_2, sum |u(t0)|_2,
+// sum |T*(t) - T*(t0)|, sum |T*(t0)| over the nodes, against the snapshot of
+// (u, v, T*) taken at the previous check, which is then replaced by the
+// current fields.  Partial sums per block in slots 0..3 (the others zero).
+template <typename S>
+__global__ void __launch_bounds__(256)
+    k_steady(const S* __restrict__ s, P2<typename Store<S>::R> p, double gbeta, double Ts,
+             double T0, double dT, double* snap, double* partial) {
+  double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  const long long nodes = (long long)p.nx * p.ny;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nodes;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(k / p.nx), x = (int)(k - (long long)y * p.nx);
+    const NodeState n = node_state(s, (size_t)y * p.pitch + x, p.plane, gbeta, Ts, T0);
+    const double Tn = (n.T - T0) / dT;
+    const double ou = snap[k], ov = snap[nodes + k], oT = snap[2 * nodes + k];
+    a0 += sqrt((n.ux - ou) * (n.ux - ou) + (n.uy - ov) * (n.uy - ov));
+    a1 += sqrt(ou * ou + ov * ov);
+    a2 += fabs(Tn - oT);
+    a3 += fabs(oT);
+    snap[k] = n.ux;
+    snap[nodes + k] = n.uy;
+    snap[2 * nodes + k] = Tn;
+  }
+  __shared__ double sh[8][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); a3 = warp_sum(a3);
+  if (lane == 0) { sh[warp][0] = a0; sh[warp][1] = a1; sh[warp][2] = a2; sh[warp][3] = a3; }
+  __syncthreads();
+  if (threadIdx.x < RED_STRIDE) {
+    double v = 0.0;
+    if (threadIdx.x < 4)
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
+    partial[(size_t)blockIdx.x * RED_STRIDE + threadIdx.x] = v;
   }
 }
 
@@ -412,7 +453,8 @@ P2<R> make_params(const Solver& s) {
   }
   const Physics& h = s.ph;
   p.gbeta = R(h.gbeta);
-  p.T0 = R(h.T0);
+  p.Ts = R(h.Ts);
+  p.Fb = R(h.Ts - h.T0);
   p.s_e = R(h.s_e);
   p.s_eps = R(h.s_eps);
   p.s_q = R(h.s_q);
@@ -421,8 +463,8 @@ P2<R> make_params(const Solver& s) {
   p.q_e = R(h.q_e);
   p.q_nu = R(h.q_nu);
   p.a_T = R(h.a_T);
-  p.abb_hot = R(h.omega * (h.T_hot - h.T0));
-  p.abb_cold = R(h.omega * (h.T_cold - h.T0));
+  p.abb_hot = R(h.omega * (h.T_hot - h.Ts));
+  p.abb_cold = R(h.omega * (h.T_cold - h.Ts));
   return p;
 }
 
@@ -881,7 +923,7 @@ struct FieldsFn {
   static cudaError_t run(Solver& s, double* rho, double* T, double* u, double* v) {
     using R = typename Store<S>::R;
     k_fields<S><<<grid2(s), block2(), 0, s.stream>>>(static_cast<const S*>(s.buf[s.cur]),
-                                                    make_params<R>(s), s.ph.gbeta, s.ph.T0, rho,
+                                                    make_params<R>(s), s.ph.gbeta, s.ph.Ts, s.ph.T0, rho,
                                                     T, u, v);
     return cudaGetLastError();
   }
@@ -902,8 +944,19 @@ struct ReduceFn {
   static cudaError_t run(Solver& s) {
     using R = typename Store<S>::R;
     k_reduce<S><<<s.red_blocks, 256, 0, s.stream>>>(
-        static_cast<const S*>(s.buf[s.cur]), make_params<R>(s), s.ph.gbeta, s.ph.T0,
+        static_cast<const S*>(s.buf[s.cur]), make_params<R>(s), s.ph.gbeta, s.ph.Ts, s.ph.T0,
         s.dax[0].W, s.dax[1].W, s.dscratch);
+    return cudaGetLastError();
+  }
+};
+
+template <typename S>
+struct SteadyFn {
+  static cudaError_t run(Solver& s) {
+    using R = typename Store<S>::R;
+    k_steady<S><<<s.red_blocks, 256, 0, s.stream>>>(
+        static_cast<const S*>(s.buf[s.cur]), make_params<R>(s), s.ph.gbeta, s.ph.Ts, s.ph.T0,
+        s.ph.dT, s.dsnap, s.dscratch);
     return cudaGetLastError();
   }
 };
@@ -941,6 +994,12 @@ cudaError_t launch_populations(Solver& s, double* f, double* g) {
 
 cudaError_t launch_reduce(Solver& s) {
   cudaError_t e = (s.dim == 3) ? launch_reduce_3d(s) : dispatch<ReduceFn>(s);
+  if (e != cudaSuccess) return e;
+  return launch_finish_reduce(s);
+}
+
+cudaError_t launch_steady(Solver& s) {
+  cudaError_t e = (s.dim == 3) ? launch_steady_3d(s) : dispatch<SteadyFn>(s);
   if (e != cudaSuccess) return e;
   return launch_finish_reduce(s);
 }

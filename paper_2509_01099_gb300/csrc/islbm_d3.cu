@@ -22,7 +22,9 @@ struct P3 {
   long long plane;
   const int* b[3][2];
   const R* w[3][2];
-  R gbeta, T0, s_e, s_eps, s_q, s_nu, s_pi, s_m, q_j, q_e, q_nu, a_T;
+  // temperature populations carry T - T_s; force rho g beta (T - T_s + Fb)
+  R gbeta, s_e, s_eps, s_q, s_nu, s_pi, s_m, q_j, q_e, q_nu, a_T;
+  R Ts, Fb;
   R abb_hot, abb_cold;
 };
 
@@ -56,8 +58,8 @@ __device__ __forceinline__ void collide3(R (&f)[19], R (&g)[7], const P3<R>& p, 
   const R jy = (f[3] - f[4]) + xy_y + yz_y;
   const R jz = (f[5] - f[6]) + xz_z + yz_z;
   const R Tr = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
-  const R T = Tr + p.T0;
-  const R Fy = rho * p.gbeta * Tr;
+  const R T = Tr;   // T - T_s
+  const R Fy = rho * p.gbeta * (Tr + p.Fb);
   const R inv = R(1) / rho;
   const R ux = jx * inv, uy = (jy + R(0.5) * Fy) * inv, uz = jz * inv;
   const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
@@ -283,7 +285,7 @@ __global__ void k_init_fields3(S* __restrict__ fout, P3<typename Store<S>::R> p,
   if (x >= p.nx || y >= p.ny) return;
   const size_t node = ((size_t)z * p.ny + y) * p.nx + x;
   const R rho = rho_in ? R(rho_in[node]) : R(1);
-  const R T = R(T_in[node]);
+  const R T = R(T_in[node] - (double)p.Ts);   // T - T_s
   const R ux = u_in ? R(u_in[node]) : R(0);
   const R uy = v_in ? R(v_in[node]) : R(0);
   const R uz = w_in ? R(w_in[node]) : R(0);
@@ -295,7 +297,7 @@ __global__ void k_init_fields3(S* __restrict__ fout, P3<typename Store<S>::R> p,
     f[i] = wrest3<R>(i) * (rho * (R(1) + R(3) * eu + R(4.5) * eu * eu - R(1.5) * usq) - R(1));
   }
   const R t0 = (R(1) - p.a_T) / R(7), ti = (R(6) + p.a_T) / R(42);
-  const R Tr = T - p.T0;
+  const R Tr = T;
   g[0] = t0 * Tr;
 #pragma unroll
   for (int i = 1; i < 7; ++i)
@@ -319,12 +321,11 @@ __global__ void k_init_pops3(S* __restrict__ fout, P3<typename Store<S>::R> p,
   if (x >= p.nx || y >= p.ny) return;
   const size_t nodes = (size_t)p.nx * p.ny * p.nz;
   const size_t node = ((size_t)z * p.ny + y) * p.nx + x;
-  const R t0 = (R(1) - p.a_T) / R(7), ti = (R(6) + p.a_T) / R(42);
   R f[19], g[7];
 #pragma unroll
   for (int i = 0; i < 19; ++i) f[i] = R(fin[i * nodes + node] - wrest3<double>(i));
 #pragma unroll
-  for (int i = 0; i < 7; ++i) g[i] = R(gin[i * nodes + node]) - (i == 0 ? t0 : ti) * p.T0;
+  for (int i = 0; i < 7; ++i) g[i] = R(gin[i * nodes + node]);
   R r_, a_, b_, c_, d_;
   collide3(f, g, p, r_, a_, b_, c_, d_);
   const size_t idx = ((size_t)z * p.ny + y) * p.pitch + x;
@@ -340,7 +341,8 @@ struct NodeState3 {
 
 template <typename S>
 __device__ __forceinline__ NodeState3 node_state3(const S* __restrict__ s, size_t idx,
-                                                  long long P, double gbeta, double T0) {
+                                                  long long P, double gbeta, double Ts,
+                                                  double Tref) {
   double f[19], g[7];
 #pragma unroll
   for (int i = 0; i < 19; ++i) f[i] = (double)Store<S>::ld(s + i * P + idx);
@@ -358,8 +360,8 @@ __device__ __forceinline__ NodeState3 node_state3(const S* __restrict__ s, size_
   for (int i = 0; i < 7; ++i) Tr += g[i];
   NodeState3 n;
   n.rho = 1.0 + drho;
-  n.T = Tr + T0;
-  const double Fy = n.rho * gbeta * Tr;
+  n.T = Tr + Ts;
+  const double Fy = n.rho * gbeta * (n.T - Tref);
   n.ux = jx / n.rho;
   n.uy = (jy - 0.5 * Fy) / n.rho;
   n.uz = jz / n.rho;
@@ -368,12 +370,14 @@ __device__ __forceinline__ NodeState3 node_state3(const S* __restrict__ s, size_
 
 template <typename S>
 __global__ void k_fields3(const S* __restrict__ s, P3<typename Store<S>::R> p, double gbeta,
-                          double T0, double* rho, double* T, double* u, double* v, double* w) {
+                          double Ts, double Tref, double* rho, double* T, double* u, double* v,
+                          double* w) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= p.nx || y >= p.ny) return;
-  const NodeState3 n = node_state3(s, ((size_t)z * p.ny + y) * p.pitch + x, p.plane, gbeta, T0);
+  const NodeState3 n =
+      node_state3(s, ((size_t)z * p.ny + y) * p.pitch + x, p.plane, gbeta, Ts, Tref);
   const size_t node = ((size_t)z * p.ny + y) * p.nx + x;
   if (rho) rho[node] = n.rho;
   if (T) T[node] = n.T;
@@ -392,21 +396,19 @@ __global__ void k_pops3(const S* __restrict__ s, P3<typename Store<S>::R> p, dou
   const size_t nodes = (size_t)p.nx * p.ny * p.nz;
   const size_t node = ((size_t)z * p.ny + y) * p.nx + x;
   const size_t idx = ((size_t)z * p.ny + y) * p.pitch + x;
-  const double t0 = (1.0 - (double)p.a_T) / 7.0, ti = (6.0 + (double)p.a_T) / 42.0;
 #pragma unroll
   for (int i = 0; i < 19; ++i)
     f[i * nodes + node] = (double)Store<S>::ld(s + i * p.plane + idx) + wrest3<double>(i);
 #pragma unroll
-  for (int i = 0; i < 7; ++i)
-    g[i * nodes + node] =
-        (double)Store<S>::ld(s + (19 + i) * p.plane + idx) + (i == 0 ? t0 : ti) * (double)p.T0;
+  for (int i = 0; i < 7; ++i) g[i * nodes + node] = (double)Store<S>::ld(s + (19 + i) * p.plane + idx);
 }
 
 // FP64 reductions (Sec. 4): volume sums and the wall-plane temperature sums of
 // Eq. (17) with the wall-plane weights W_y W_z.
 template <typename S>
 __global__ void __launch_bounds__(256)
-    k_reduce3(const S* __restrict__ s, P3<typename Store<S>::R> p, double gbeta, double T0,
+    k_reduce3(const S* __restrict__ s, P3<typename Store<S>::R> p, double gbeta, double Ts,
+              double T0,
               const double* __restrict__ Wx, const double* __restrict__ Wy,
               const double* __restrict__ Wz, double* partial) {
   double acc[RED_COUNT];
@@ -418,7 +420,8 @@ __global__ void __launch_bounds__(256)
     const int x = (int)(k % p.nx);
     const long long r = k / p.nx;
     const int y = (int)(r % p.ny), z = (int)(r / p.ny);
-    const NodeState3 n = node_state3(s, ((size_t)z * p.ny + y) * p.pitch + x, p.plane, gbeta, T0);
+    const NodeState3 n =
+        node_state3(s, ((size_t)z * p.ny + y) * p.pitch + x, p.plane, gbeta, Ts, T0);
     const double wp = Wy[y] * Wz[z];
     const double W = Wx[x] * wp;
     const double u2 = n.ux * n.ux + n.uy * n.uy + n.uz * n.uz;
@@ -427,7 +430,7 @@ __global__ void __launch_bounds__(256)
     acc[RED_MASS] += W * n.rho;
     acc[RED_UT] += W * n.ux * Tr;
     acc[RED_SPEED] += W * sp;
-    acc[RED_SPEED_UV] += W * sqrt(n.ux * n.ux + n.uy * n.uy);
+    acc[RED_UV2] += W * (n.ux * n.ux + n.uy * n.uy);
     acc[RED_U2] += W * u2;
     if (x == 0) acc[RED_HOT1] += wp * n.T;
     if (x == 1) acc[RED_HOT2] += wp * n.T;
@@ -455,6 +458,45 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Steady-state criterion (Sec. 3) in 3-D, as the 2-D kernel with (u, v, w, T*).
+template <typename S>
+__global__ void __launch_bounds__(256)
+    k_steady3(const S* __restrict__ s, P3<typename Store<S>::R> p, double gbeta, double Ts,
+              double T0, double dT, double* snap, double* partial) {
+  double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  const long long nodes = (long long)p.nx * p.ny * p.nz;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nodes;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(k % p.nx);
+    const long long r = k / p.nx;
+    const int y = (int)(r % p.ny), z = (int)(r / p.ny);
+    const NodeState3 n =
+        node_state3(s, ((size_t)z * p.ny + y) * p.pitch + x, p.plane, gbeta, Ts, T0);
+    const double Tn = (n.T - T0) / dT;
+    const double ou = snap[k], ov = snap[nodes + k], ow = snap[2 * nodes + k];
+    const double oT = snap[3 * nodes + k];
+    a0 += sqrt((n.ux - ou) * (n.ux - ou) + (n.uy - ov) * (n.uy - ov) + (n.uz - ow) * (n.uz - ow));
+    a1 += sqrt(ou * ou + ov * ov + ow * ow);
+    a2 += fabs(Tn - oT);
+    a3 += fabs(oT);
+    snap[k] = n.ux;
+    snap[nodes + k] = n.uy;
+    snap[2 * nodes + k] = n.uz;
+    snap[3 * nodes + k] = Tn;
+  }
+  __shared__ double sh[8][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); a3 = warp_sum(a3);
+  if (lane == 0) { sh[warp][0] = a0; sh[warp][1] = a1; sh[warp][2] = a2; sh[warp][3] = a3; }
+  __syncthreads();
+  if (threadIdx.x < RED_STRIDE) {
+    double v = 0.0;
+    if (threadIdx.x < 4)
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
+    partial[(size_t)blockIdx.x * RED_STRIDE + threadIdx.x] = v;
+  }
+}
+
 template <typename R>
 P3<R> make_params3(const Solver& s) {
   P3<R> p;
@@ -470,7 +512,8 @@ P3<R> make_params3(const Solver& s) {
     }
   const Physics& h = s.ph;
   p.gbeta = R(h.gbeta);
-  p.T0 = R(h.T0);
+  p.Ts = R(h.Ts);
+  p.Fb = R(h.Ts - h.T0);
   p.s_e = R(h.s_e);
   p.s_eps = R(h.s_eps);
   p.s_q = R(h.s_q);
@@ -481,8 +524,8 @@ P3<R> make_params3(const Solver& s) {
   p.q_e = R(h.q_e);
   p.q_nu = R(h.q_nu);
   p.a_T = R(h.a_T);
-  p.abb_hot = R(h.omega * (h.T_hot - h.T0));
-  p.abb_cold = R(h.omega * (h.T_cold - h.T0));
+  p.abb_hot = R(h.omega * (h.T_hot - h.Ts));
+  p.abb_cold = R(h.omega * (h.T_cold - h.Ts));
   return p;
 }
 
@@ -541,8 +584,8 @@ struct Fields3 {
   static cudaError_t run(Solver& s, double* rho, double* T, double* u, double* v, double* w) {
     using R = typename Store<S>::R;
     k_fields3<S><<<grid3(s), block3(), 0, s.stream>>>(static_cast<const S*>(s.buf[s.cur]),
-                                                     make_params3<R>(s), s.ph.gbeta, s.ph.T0,
-                                                     rho, T, u, v, w);
+                                                     make_params3<R>(s), s.ph.gbeta, s.ph.Ts,
+                                                     s.ph.T0, rho, T, u, v, w);
     return cudaGetLastError();
   }
 };
@@ -562,8 +605,19 @@ struct Reduce3 {
   static cudaError_t run(Solver& s) {
     using R = typename Store<S>::R;
     k_reduce3<S><<<s.red_blocks, 256, 0, s.stream>>>(
-        static_cast<const S*>(s.buf[s.cur]), make_params3<R>(s), s.ph.gbeta, s.ph.T0,
+        static_cast<const S*>(s.buf[s.cur]), make_params3<R>(s), s.ph.gbeta, s.ph.Ts, s.ph.T0,
         s.dax[0].W, s.dax[1].W, s.dax[2].W, s.dscratch);
+    return cudaGetLastError();
+  }
+};
+
+template <typename S>
+struct Steady3 {
+  static cudaError_t run(Solver& s) {
+    using R = typename Store<S>::R;
+    k_steady3<S><<<s.red_blocks, 256, 0, s.stream>>>(
+        static_cast<const S*>(s.buf[s.cur]), make_params3<R>(s), s.ph.gbeta, s.ph.Ts, s.ph.T0,
+        s.ph.dT, s.dsnap, s.dscratch);
     return cudaGetLastError();
   }
 };
@@ -595,5 +649,7 @@ cudaError_t launch_populations_3d(Solver& s, double* f, double* g) {
 }
 
 cudaError_t launch_reduce_3d(Solver& s) { return dispatch3<Reduce3>(s); }
+
+cudaError_t launch_steady_3d(Solver& s) { return dispatch3<Steady3>(s); }
 
 }  // namespace islbm

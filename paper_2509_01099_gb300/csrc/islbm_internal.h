@@ -16,7 +16,7 @@ enum RedSlot {
   RED_MASS = 0,   // sum rho W
   RED_UT,         // sum u (T - T0) W
   RED_SPEED,      // sum |u| W
-  RED_SPEED_UV,   // sum sqrt(u^2 + v^2) W
+  RED_UV2,        // sum (u^2 + v^2) W
   RED_U2,         // sum |u|^2 W
   RED_HOT1,       // sum T W_perp on the first fluid plane next to the hot wall
   RED_HOT2,       // ... on the second plane
@@ -67,7 +67,8 @@ struct Physics {
   double Ra, Pr, Ma, L, u_f, nu, alpha, gbeta, dT;
   double s_nu, s_e, s_eps, s_q, s_pi, s_m;
   double q_j, q_e, q_nu, a_T, omega;
-  double T_hot, T_cold, T0;
+  double T_hot, T_cold, T0;   // T0: reference of the buoyancy force and of T*
+  double Ts;                  // storage offset of the temperature populations (mean wall T)
   // wall-derivative coefficients (Eq. (17)): dT/dX = cw*T_w + c1*T_1 + c2*T_2
   double hot_cw, hot_c1, hot_c2, cold_cw, cold_c1, cold_c2;
   double mid_inv_dx;  // 1/(X_{m+1}-X_m) (even n) or 1/(X_{m+1}-X_{m-1}) (odd n)
@@ -96,6 +97,8 @@ struct Solver {
   double* dresult = nullptr;      // finished reduction vector
   double* hresult = nullptr;      // pinned host copy
   double* dfield = nullptr;       // staging for field upload / download (5 * nodes)
+  double* dsnap = nullptr;        // steady-state snapshot (u, v[, w], T*), allocated on first use
+  bool snap_valid = false;
   std::string err;
   unsigned long long fingerprint = 0;
   int variant = KV_DIRECT;        // step kernel of the 2-D FP32/16-bit path
@@ -131,6 +134,9 @@ cudaError_t launch_reduce_3d(Solver& s);
 
 // Deterministic final sum of the per-block partials (islbm_d2.cu).
 cudaError_t launch_finish_reduce(Solver& s);
+// Steady-state sums against the snapshot (which is then refreshed); slots 0..3 of dresult.
+cudaError_t launch_steady(Solver& s);
+cudaError_t launch_steady_3d(Solver& s);
 
 }  // namespace islbm
 

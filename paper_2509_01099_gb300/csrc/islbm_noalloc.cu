@@ -22,7 +22,7 @@ constexpr int kNodesPerBlock = 16384;   // nodes reduced by one block
 constexpr int kMaxBlocks = 8192;        // partial rows in the scratch array
 constexpr long long kMaxNodes = (long long)kNodesPerBlock * kMaxBlocks;   // 134,217,728
 constexpr int kRow = islbm::RED_STRIDE;  // doubles per partial row
-constexpr int kResults = 10;            // finished values written by the last kernel
+constexpr int kResults = 11;            // finished values written by the last kernel
 constexpr int kMaxDevices = 64;
 
 // 8193 rows of 16 doubles: the partials of at most kMaxBlocks blocks, then the
@@ -38,7 +38,7 @@ double* g_scratch_ptr[kMaxDevices] = {nullptr};
 __global__ void __launch_bounds__(256)
     k_noalloc_partials(const double* __restrict__ f, const double* __restrict__ g, int nx,
                        int ny, const double* __restrict__ xi_x, const double* __restrict__ xi_y,
-                       double u_f, double T0, double* scratch) {
+                       double u_f, double Ts, double T0, double* scratch) {
   using namespace islbm;
   double acc[RED_COUNT];
 #pragma unroll
@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(256)
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i) T += g[(size_t)i * nodes + k];
+    T += Ts;                      // the populations carry T - T_s
     const double Tr = T - T0;
     const double Fy = rho * gbeta * Tr;
     const double ux = jx / rho, uy = (jy - 0.5 * Fy) / rho;
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(256)
     acc[RED_MASS] += W * rho;
     acc[RED_UT] += W * ux * Tr;
     acc[RED_SPEED] += W * sp;
-    acc[RED_SPEED_UV] += W * sp;
+    acc[RED_UV2] += W * u2;
     acc[RED_U2] += W * u2;
     if (x == 0) acc[RED_HOT1] += wy * T;
     if (x == 1) acc[RED_HOT2] += wy * T;
@@ -152,8 +153,9 @@ __global__ void k_noalloc_finish(double* scratch, int blocks, int nx, int ny,
                             : 1.0 / (X(xi_x, (nx + 1) / 2 + 1) - X(xi_x, (nx + 1) / 2 - 1));
   res[3] = (sq * sums[RED_MIDCONV] / (ph.u_f * ph.dT) -
             L * (sums[RED_MIDTR] - sums[RED_MIDTL]) * inv_dx / ph.dT) / L;
-  res[4] = sqrt(ph.Ra / ph.Pr) * sums[RED_SPEED] / (ph.u_f * vol);
-  res[5] = sqrt(ph.Ra / ph.Pr) * sums[RED_SPEED_UV] / (ph.u_f * vol);
+  res[4] = sqrt(ph.Ra / ph.Pr) * sqrt(sums[RED_U2] / vol) / ph.u_f;
+  res[5] = sqrt(ph.Ra / ph.Pr) * sqrt(sums[RED_UV2] / vol) / ph.u_f;
+  res[10] = sqrt(ph.Ra / ph.Pr) * sums[RED_SPEED] / (ph.u_f * vol);
   res[6] = sums[RED_MASS];
   res[7] = 0.5 * sums[RED_U2];
   res[8] = sums[RED_MAXSPEED] / ph.u_f;
@@ -218,9 +220,10 @@ extern "C" islbm_status islbm_reduce_noalloc(const double* f, const double* g, i
   ph.u_f = u_f;
   ph.T_hot = prm.T_hot;
   ph.T_cold = prm.T_cold;
-  ph.T0 = 0.5 * (prm.T_hot + prm.T_cold);
+  ph.T0 = prm.reference == ISLBM_TREF_COLD ? prm.T_cold : 0.5 * (prm.T_hot + prm.T_cold);
   ph.dT = prm.T_hot != prm.T_cold ? prm.T_hot - prm.T_cold : 1.0;
-  k_noalloc_partials<<<blocks, 256, 0, st>>>(f, g, nx, ny, xi_x, xi_y, u_f, ph.T0, scratch);
+  k_noalloc_partials<<<blocks, 256, 0, st>>>(f, g, nx, ny, xi_x, xi_y, u_f,
+                                             0.5 * (prm.T_hot + prm.T_cold), ph.T0, scratch);
   k_noalloc_finish<<<1, 32 * islbm::RED_COUNT, 0, st>>>(scratch, blocks, nx, ny, xi_x, xi_y, ph);
   double res[kResults];
   if (cudaGetLastError() != cudaSuccess ||
@@ -241,6 +244,7 @@ extern "C" islbm_status islbm_reduce_noalloc(const double* f, const double* g, i
   out->ke = res[7];
   out->max_speed = res[8];
   out->nonfinite = res[9];
+  out->Re_mean = res[10];
   if (res[9] > 0 || !std::isfinite(res[0])) {
     set_last_error_static("islbm_reduce_noalloc: non-finite values in the state");
     return ISLBM_ERR_DIVERGED;

@@ -18,6 +18,7 @@ from . import build as _build
 LATTICES = {"d2q9_d2q5": 0, "d3q19_d3q7": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16dev": 2, "bf16dev": 3}
 STENCILS = {"centred": 0, "upwind": 1}
+REFERENCES = {"mean": 0, "cold": 1}
 KERNELS = {"auto": 0, "direct": 1, "tiled": 2, "tma_r4s2": 3, "tma_r2s2": 4, "tma_r2s3": 5,
            "tma_r4s3": 6}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_DIVERGED",
@@ -30,7 +31,7 @@ EXPORTS = (
     "islbm_set_fields", "islbm_set_fields_device", "islbm_set_populations", "islbm_step",
     "islbm_get_fields", "islbm_get_fields_device", "islbm_get_populations", "islbm_reduce",
     "islbm_nusselt", "islbm_reynolds", "islbm_mass", "islbm_synchronize", "islbm_save",
-    "islbm_load", "islbm_reduce_noalloc",
+    "islbm_load", "islbm_reduce_noalloc", "islbm_steady_change", "islbm_run_to_steady",
 )
 
 
@@ -45,7 +46,8 @@ class Params(ctypes.Structure):
                 ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
                 ("s_pi", ctypes.c_double), ("s_m", ctypes.c_double), ("q_j", ctypes.c_double),
                 ("q_e", ctypes.c_double), ("q_nu", ctypes.c_double), ("stencil", ctypes.c_int),
-                ("kernel", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("kernel", ctypes.c_int), ("reference", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class Info(ctypes.Structure):
@@ -60,7 +62,7 @@ class Info(ctypes.Structure):
 
 class Reductions(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
-                ("Nu", "Nu_hot", "Nu_cold", "Nu_middle", "Re", "Re_uv", "mass", "ke",
+                ("Nu", "Nu_hot", "Nu_cold", "Nu_middle", "Re", "Re_uv", "Re_mean", "mass", "ke",
                  "max_speed", "nonfinite")] + [("time", ctypes.c_longlong)]
 
 
@@ -115,6 +117,9 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
         "islbm_save": (i, [h, ctypes.c_char_p]),
         "islbm_load": (i, [h, ctypes.c_char_p]),
         "islbm_reduce_noalloc": (i, [vp, vp, i, i, vp, vp, d, d, P(Params), vp, P(Reductions)]),
+        "islbm_steady_change": (i, [h, dp, dp]),
+        "islbm_run_to_steady": (i, [h, d, ctypes.c_longlong, ctypes.c_longlong,
+                                    P(ctypes.c_longlong), dp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -294,6 +299,22 @@ def islbm_mass(h) -> float:
     return x.value
 
 
+def islbm_steady_change(h):
+    du, dT = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().islbm_steady_change(h, ctypes.byref(du), ctypes.byref(dT)), h)
+    return du.value, dT.value
+
+
+def islbm_run_to_steady(h, tol=1e-9, interval=2000, max_steps=10_000_000, check=True):
+    steps, du, dT = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+    st = load_library().islbm_run_to_steady(h, float(tol), int(interval), int(max_steps),
+                                             ctypes.byref(steps), ctypes.byref(du),
+                                             ctypes.byref(dT))
+    if check:
+        _check(st, h)
+    return {"steps": steps.value, "du": du.value, "dT": dT.value, "status": st}
+
+
 def islbm_synchronize(h):
     _check(load_library().islbm_synchronize(h), h)
 
@@ -333,7 +354,7 @@ class Solver:
             params = params if params is not None else islbm_default_params()
             for k, v in overrides.items():
                 if isinstance(v, str):
-                    v = {"stencil": STENCILS, "kernel": KERNELS}[k][v]
+                    v = {"stencil": STENCILS, "kernel": KERNELS, "reference": REFERENCES}[k][v]
                 setattr(params, k, v)
         self.h = islbm_create(xi_x, xi_y, xi_z, Ra, Pr, None, precision, params, stream)
         self.info = islbm_info(self.h)
@@ -388,6 +409,12 @@ class Solver:
 
     def synchronize(self):
         islbm_synchronize(self.h)
+
+    def steady_change(self):
+        return islbm_steady_change(self.h)
+
+    def run_to_steady(self, tol=1e-9, interval=2000, max_steps=10_000_000, check=True):
+        return islbm_run_to_steady(self.h, tol, interval, max_steps, check)
 
     def save(self, path):
         islbm_save(self.h, path)

@@ -76,7 +76,9 @@ def test_cavity_fields_after_1000_steps(mesh, precision):
         assert rel_field_error(got[k], ref[k]) <= 3 * TOL[precision], k
     assert np.abs(got["rho"] - ref["rho"]).max() <= 10 * TOL[precision]
     for k in ("Nu", "Nu_hot", "Nu_cold", "Nu_middle", "Re"):
-        r = abs(got["red"][k] - ref["red"][k]) / abs(ref["red"][k])
+        # Nusselt numbers are O(1) (conduction: 1); early in a run Nu_middle is
+        # near zero, so the bound is taken on that scale
+        r = abs(got["red"][k] - ref["red"][k]) / max(1.0, abs(ref["red"][k]))
         assert r <= NU_TOL[precision], (k, got["red"][k], ref["red"][k])
     assert abs(got["red"]["mass"] / ref["red"]["mass"] - 1) <= NU_TOL[precision]
 
