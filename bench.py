@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--kernel", default="auto", help="step-kernel variant (library default: auto)")
     ap.add_argument("--sweep", action="store_true",
                     help="time every kernel variant and storage type; print one JSON line each")
+    ap.add_argument("--steady", action="store_true",
+                    help="wall time to the steady state per storage type (256^2 tanh mesh)")
+    ap.add_argument("--sweep3d", action="store_true", help="time the 3-D step (256^3)")
     return ap.parse_args()
 
 
@@ -244,6 +247,51 @@ def sweep(args, pkg, torch, flush):
                     s.close()
 
 
+def steady(args, pkg, torch):
+    """Wall time until the steady criterion of Sec. 3 holds, per storage type, on
+    the 256^2 tanh-stretched cavity (a = 1.5) at Ra = 1e7, from rest; the
+    criterion is 1e-7 for FP32 and 1e-5 for the 16-bit forms over 2000 steps."""
+    from synthetic import temperature_noise
+    n, Ra = 256, 1e7
+    out = {}
+    for prec, tol in (("fp32", 1e-7), ("fp16dev", 1e-5), ("bf16dev", 1e-5)):
+        s = make_solver(pkg, n, "tanh", Ra, prec)
+        s.set_fields(temperature_noise(s.shape, 1e-6, seed=0))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = s.run_to_steady(tol=tol, interval=2000, max_steps=4_000_000, check=False)
+        red = s.reduce(check=False)
+        wall = time.perf_counter() - t0
+        out[prec] = {"steps": r["steps"], "wall_s": wall, "converged": r["status"] == 0,
+                     "du": r["du"], "dT": r["dT"], "Nu": red["Nu"], "Nu_hot": red["Nu_hot"],
+                     "Re": red["Re"], "tf": r["steps"] / s.info.steps_per_tf,
+                     "MLUPS": n * n * r["steps"] / (wall * 1e6)}
+        s.close()
+    for prec in ("fp16dev", "bf16dev"):
+        out[prec]["Nu_rel_to_fp32"] = out[prec]["Nu"] / out["fp32"]["Nu"] - 1
+        out[prec]["wall_rel_to_fp32"] = out[prec]["wall_s"] / out["fp32"]["wall_s"]
+    print(json.dumps({"steady": True, "workload": f"2-D cavity {n}^2 tanh a=1.5, Ra={Ra:g}",
+                      "results": out}), flush=True)
+
+
+def sweep3d(args, pkg, torch, flush):
+    """The 3-D step (D3Q19 + D3Q7) on the 256^3 tanh mesh and the uniform mesh."""
+    n = 256
+    for mesh in ("tanh", "uniform"):
+        for prec in ("fp32", "bf16dev"):
+            xi = pkg.islbm_mesh_uniform(n) if mesh == "uniform" else pkg.islbm_mesh_tanh(n, 1.5)
+            s = pkg.Solver(xi, xi, xi, Ra=1e7, precision=prec)
+            steps = 20
+            t = timed_steps(pkg, s, steps, 3, flush, torch)
+            nodes = n ** 3
+            b = 2 * 26 * BYTES_PER_VALUE[prec]
+            print(json.dumps({"sweep3d": True, "n": n, "mesh": mesh, "precision": prec,
+                              "kernel": s.info.kernel, "MLUPS": nodes * steps / (t * 1e6),
+                              "GBps": b * nodes / (t / steps) / 1e9,
+                              "us_per_step": 1e6 * t / steps}), flush=True)
+            s.close()
+
+
 def flush_l2(flush):
     """Write a 256 MB buffer (evicts everything the previous step left in the
     126 MB L2), then read a second 256 MB buffer, so the write-backs of the
@@ -297,6 +345,12 @@ def main():
              torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")]
     if args.sweep:
         sweep(args, pkg, torch, flush)
+        return
+    if args.steady:
+        steady(args, pkg, torch)
+        return
+    if args.sweep3d:
+        sweep3d(args, pkg, torch, flush)
         return
     solver = make_solver(pkg, n, args.mesh, args.Ra, args.precision, args.kernel)
     info = solver.info

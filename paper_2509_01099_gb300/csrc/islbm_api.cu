@@ -512,6 +512,14 @@ extern "C" void islbm_destroy(islbm_t s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
   for (int b = 0; b < 2; ++b)
+    if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
+  if (s->side) {
+    cudaStreamSynchronize(s->side);
+    cudaStreamDestroy(s->side);
+  }
+  if (s->ev_in) cudaEventDestroy(s->ev_in);
+  if (s->ev_out) cudaEventDestroy(s->ev_out);
+  for (int b = 0; b < 2; ++b)
     if (s->buf[b]) cudaFree(s->buf[b]);
   if (s->dtables) cudaFree(s->dtables);
   if (s->dscratch) cudaFree(s->dscratch);
@@ -620,9 +628,62 @@ extern "C" islbm_status islbm_set_populations(islbm_t s, const double* f, const 
   return ISLBM_OK;
 }
 
+// Capture kGraphSteps consecutive steps starting from buffer `parity` into a
+// graph on the private stream.
+static cudaError_t build_graph(Solver* s, int parity) {
+  cudaError_t e;
+  if (!s->side) {
+    e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  const cudaStream_t user = s->stream;
+  const int cur = s->cur;
+  const long long t0 = s->time;
+  s->stream = s->side;
+  s->cur = parity;
+  e = cudaStreamBeginCapture(s->side, cudaStreamCaptureModeThreadLocal);
+  cudaError_t le = cudaSuccess;
+  if (e == cudaSuccess) {
+    // each captured step gets its own step index (it seeds the stochastic
+    // rounding of 16-bit stores; replays repeat the 64 indices)
+    for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k, ++s->time) le = launch_step(*s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s->side, &g);
+    if (e == cudaSuccess && le == cudaSuccess) e = cudaGraphInstantiate(&s->graph[parity], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (le != cudaSuccess) e = le;
+  }
+  s->stream = user;
+  s->cur = cur;
+  s->time = t0;
+  return e;
+}
+
 extern "C" islbm_status islbm_step(islbm_t s, long long n) {
   if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_step: NULL handle");
   if (n < 0) return fail(s, ISLBM_ERR_ARG, "islbm_step: negative step count");
+  // whole blocks of kGraphSteps steps are replayed from a captured graph
+  while (s->use_graphs && n >= kGraphSteps) {
+    if (!s->graph[s->cur]) {
+      const cudaError_t e = build_graph(s, s->cur);
+      if (e != cudaSuccess) {   // fall back to plain launches for this handle
+        s->use_graphs = false;
+        cudaGetLastError();
+        break;
+      }
+    }
+    CK(s, cudaEventRecord(s->ev_in, s->stream));
+    CK(s, cudaStreamWaitEvent(s->side, s->ev_in, 0));
+    CK(s, cudaGraphLaunch(s->graph[s->cur], s->side));
+    CK(s, cudaEventRecord(s->ev_out, s->side));
+    CK(s, cudaStreamWaitEvent(s->stream, s->ev_out, 0));
+    n -= kGraphSteps;
+    s->time += kGraphSteps;
+  }
   for (long long k = 0; k < n; ++k) {
     CK(s, launch_step(*s));
     ++s->time;

@@ -37,6 +37,7 @@ struct P2 {
   R gbeta, s_e, s_eps, s_q, s_nu, q_j, q_e, q_nu, a_T;
   R Ts, Fb;             // T_s and T_s - T_ref
   R abb_hot, abb_cold;  // omega (T_w - T_s) of the anti-bounce-back rule
+  unsigned step;        // step counter (seeds the stochastic rounding of 16-bit stores)
 };
 
 // Rest weights w_i of the D2Q9 populations.
@@ -197,10 +198,11 @@ __global__ void __launch_bounds__(256)
 
   R rho, ux, uy, T;
   collide(f, g, p, rho, ux, uy, T);
+  unsigned r = sr_seed(idx, p.step);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) St::st(fout + i * P + idx, f[i]);
+  for (int i = 0; i < 9; ++i) St::st_sr(fout + i * P + idx, f[i], sr_next(r));
 #pragma unroll
-  for (int i = 0; i < 5; ++i) St::st(fout + (9 + i) * P + idx, g[i]);
+  for (int i = 0; i < 5; ++i) St::st_sr(fout + (9 + i) * P + idx, g[i], sr_next(r));
 }
 
 // Equilibrium (Sec. 2.1) of given fields, then the collision.  The flow
@@ -465,6 +467,7 @@ P2<R> make_params(const Solver& s) {
   p.a_T = R(h.a_T);
   p.abb_hot = R(h.omega * (h.T_hot - h.Ts));
   p.abb_cold = R(h.omega * (h.T_cold - h.Ts));
+  p.step = (unsigned)s.time;
   return p;
 }
 
@@ -654,10 +657,12 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ sm, const float4
     float rho, ux, uy, T;
     collide(fn, gn, p, rho, ux, uy, T);
     const size_t idx = (size_t)y * p.pitch + x;
+    unsigned r = sr_seed(idx, p.step);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store<S>::st(fout + (size_t)i * p.plane + idx, fn[i]);
+    for (int i = 0; i < 9; ++i) Store<S>::st_sr(fout + (size_t)i * p.plane + idx, fn[i], sr_next(r));
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Store<S>::st(fout + (size_t)(9 + i) * p.plane + idx, gn[i]);
+    for (int i = 0; i < 5; ++i)
+      Store<S>::st_sr(fout + (size_t)(9 + i) * p.plane + idx, gn[i], sr_next(r));
   }
 }
 

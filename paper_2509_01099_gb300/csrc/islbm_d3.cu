@@ -26,6 +26,7 @@ struct P3 {
   R gbeta, s_e, s_eps, s_q, s_nu, s_pi, s_m, q_j, q_e, q_nu, a_T;
   R Ts, Fb;
   R abb_hot, abb_cold;
+  unsigned step;   // seeds the stochastic rounding of 16-bit stores
 };
 
 template <typename R>
@@ -259,10 +260,11 @@ __global__ void __launch_bounds__(256)
 #undef PL
   R rho, ux, uy, uz, T;
   collide3(f, g, p, rho, ux, uy, uz, T);
+  unsigned r = sr_seed(idx, p.step);
 #pragma unroll
-  for (int i = 0; i < 19; ++i) St::st(fout + i * P + idx, f[i]);
+  for (int i = 0; i < 19; ++i) St::st_sr(fout + i * P + idx, f[i], sr_next(r));
 #pragma unroll
-  for (int i = 0; i < 7; ++i) St::st(fout + (19 + i) * P + idx, g[i]);
+  for (int i = 0; i < 7; ++i) St::st_sr(fout + (19 + i) * P + idx, g[i], sr_next(r));
 }
 
 __device__ __constant__ int kE3[19][3] = {
@@ -526,6 +528,7 @@ P3<R> make_params3(const Solver& s) {
   p.a_T = R(h.a_T);
   p.abb_hot = R(h.omega * (h.T_hot - h.Ts));
   p.abb_cold = R(h.omega * (h.T_cold - h.Ts));
+  p.step = (unsigned)s.time;
   return p;
 }
 

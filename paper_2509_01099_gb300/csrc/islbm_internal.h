@@ -105,7 +105,15 @@ struct Solver {
   int sm_count = 0;
   int* derr = nullptr;            // device error flag of the pipelined kernels
   alignas(128) unsigned char tmap[2][128];   // TMA descriptors of buf[0] / buf[1]
+  // CUDA graphs of kGraphSteps steps, one per starting buffer, replayed on a
+  // private stream that is ordered against `stream` with events
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  bool use_graphs = true;
 };
+
+constexpr int kGraphSteps = 64;   // even: a replay leaves the buffer parity unchanged
 
 // ---- kernel launchers (islbm_d2.cu / islbm_d3.cu) ----
 // Equilibrium initialisation followed by a collision; fields are device arrays

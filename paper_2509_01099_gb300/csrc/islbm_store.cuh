@@ -18,6 +18,7 @@ struct Store<double> {
   using R = double;
   static __device__ __forceinline__ R ld(const double* p) { return __ldg(p); }
   static __device__ __forceinline__ void st(double* p, R v) { *p = v; }
+  static __device__ __forceinline__ void st_sr(double* p, R v, unsigned) { *p = v; }
 };
 
 template <>
@@ -25,13 +26,38 @@ struct Store<float> {
   using R = float;
   static __device__ __forceinline__ R ld(const float* p) { return __ldg(p); }
   static __device__ __forceinline__ void st(float* p, R v) { *p = v; }
+  static __device__ __forceinline__ void st_sr(float* p, R v, unsigned) { *p = v; }
 };
+
+// Stochastic rounding of the 16-bit stores of the time step.  Near a steady
+// state the per-step change of a population (e.g. the buoyancy increment
+// g beta T w_i ~ 1e-6) is below half an FP16 / BF16 ulp of the stored
+// deviation; round-to-nearest then discards it on every step and the flow
+// stalls.  Adding uniform random bits below the kept mantissa and truncating
+// rounds up with probability equal to the discarded fraction, so the
+// expected stored value is exact.  `r` supplies 32 random bits.
+__device__ __forceinline__ float sr_to_fp16_grid(float v, unsigned r) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned sign = b & 0x80000000u;
+  unsigned mag = b & 0x7fffffffu;
+  if (mag >= 0x38800000u) {            // FP16 normal range: 13 mantissa bits are dropped
+    mag = (mag + (r >> 19)) & ~0x1fffu;
+    return __uint_as_float(mag | sign);
+  }
+  // FP16 subnormal range: the grid is 2^-24
+  const float q = 5.9604644775390625e-8f;
+  const float m = __uint_as_float(mag) + (float)(r >> 8) * (q * 5.9604644775390625e-8f);
+  return __uint_as_float(__float_as_uint(m) | sign);
+}
 
 template <>
 struct Store<__half> {
   using R = float;
   static __device__ __forceinline__ R ld(const __half* p) { return __half2float(__ldg(p)); }
   static __device__ __forceinline__ void st(__half* p, R v) { *p = __float2half_rn(v); }
+  static __device__ __forceinline__ void st_sr(__half* p, R v, unsigned r) {
+    *p = __float2half_rz(sr_to_fp16_grid(v, r));
+  }
 };
 
 template <>
@@ -43,7 +69,30 @@ struct Store<__nv_bfloat16> {
   static __device__ __forceinline__ void st(__nv_bfloat16* p, R v) {
     *p = __float2bfloat16_rn(v);
   }
+  static __device__ __forceinline__ void st_sr(__nv_bfloat16* p, R v, unsigned r) {
+    // BF16 keeps the upper 16 bits of the FP32 pattern
+    const unsigned b = __float_as_uint(v);
+    const unsigned sign = b & 0x80000000u;
+    const unsigned mag = ((b & 0x7fffffffu) + (r >> 16)) & 0xffff0000u;
+    *p = __float2bfloat16_rz(__uint_as_float(mag | sign));
+  }
 };
+
+// Random bits for the stochastic rounding: a counter-based hash of (node, step)
+// (the murmur3 finalizer), then a linear congruential sequence per store.
+__device__ __forceinline__ unsigned sr_seed(unsigned long long node, unsigned step) {
+  unsigned h = (unsigned)node * 0x9e3779b1u ^ (unsigned)(node >> 32) ^ (step * 0x85ebca77u);
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ unsigned sr_next(unsigned& r) {
+  r = r * 1664525u + 1013904223u;
+  return r;
+}
 
 // FP64 block reduction helpers shared by the reduction kernels.
 __device__ __forceinline__ double warp_sum(double v) {

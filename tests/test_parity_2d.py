@@ -97,7 +97,9 @@ def _random_state(q_f, q_g, shape, seed):
     return f, g
 
 
-POP_TOL = {"fp64": 1e-13, "fp32": 2e-6, "fp16dev": 2e-3, "bf16dev": 2e-2}
+# 16-bit stores round stochastically (error up to one ulp: 2^-10 FP16, 2^-7 BF16
+# of the stored deviation per step)
+POP_TOL = {"fp64": 1e-13, "fp32": 2e-6, "fp16dev": 5e-3, "bf16dev": 5e-2}
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16dev", "bf16dev"])
@@ -280,3 +282,23 @@ def test_default_kernel_choice():
     s = pkg.Solver(O.mesh_tanh(64, 1.5), O.mesh_tanh(64, 1.5), Ra=1e6, precision="fp64")
     assert s.info.kernel == 1
     s.close()
+
+
+@pytest.mark.parametrize("kernel", ["direct", "tma_r2s2"])
+def test_graph_replay_is_bitwise_identical(kernel):
+    """islbm_step replays blocks of 64 steps from a captured CUDA graph; the result
+    equals 64 + 64 + 7 single launches bit for bit, for both buffer parities."""
+    xi = O.mesh_tanh(48, 1.5)
+    states = []
+    for chunks in ([135], [1] * 135):
+        s = pkg.Solver(xi, xi, Ra=1e6, precision="fp32", kernel=kernel)
+        s.set_fields(temperature_noise(s.shape, 1e-6, seed=6))
+        s.step(7)                       # start the graphs from the other buffer too
+        for c in chunks:
+            s.step(c)
+        s.synchronize()
+        states.append(s.populations())
+        assert s.time == 142
+        s.close()
+    np.testing.assert_array_equal(states[0][0], states[1][0])
+    np.testing.assert_array_equal(states[0][1], states[1][1])
