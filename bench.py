@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--steady", action="store_true",
                     help="wall time to the steady state per storage type (256^2 tanh mesh)")
     ap.add_argument("--sweep3d", action="store_true", help="time the 3-D step (256^3)")
+    ap.add_argument("--batch", action="store_true",
+                    help="64-cavity Ra sweep: batched persistent launch vs a per-cavity loop")
     return ap.parse_args()
 
 
@@ -274,6 +276,62 @@ def steady(args, pkg, torch):
                       "results": out}), flush=True)
 
 
+def batch(args, pkg, torch):
+    """The batched sweep: 64 2-D cavities, Ra log-uniform in [1e6, 1e8] and
+    N from {128, 256, 384, 512} (PCG64 seed 0), tanh meshes (a = 1.5), FP32,
+    tile shapes from the autotuner.  Device time of K steps of the whole batch
+    (one persistent launch per tile shape and step, replayed from CUDA graphs)
+    against the same cavities advanced one after the other."""
+    from synthetic import ra_sweep, temperature_noise
+    ra, ns = ra_sweep(64, seed=0)
+    cavs = [dict(n=int(n), mesh="tanh", a=1.5, Ra=float(r)) for r, n in zip(ra, ns)]
+    nodes = sum(c["n"] ** 2 for c in cavities_sorted(cavs))
+    K = 640
+    t0 = time.perf_counter()
+    b = pkg.Batch(cavs, precision="fp32", autotune=True)
+    t_setup = time.perf_counter() - t0
+    for k, m in enumerate(b.members):
+        m.set_fields(temperature_noise(m.shape, 1e-6, seed=k))
+    b.step(128)
+    b.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(K)
+    e1.record(stream)
+    b.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    rows = sorted(set(b.tile_rows(k) for k in range(len(cavs))))
+    b.close()
+    # the same cavities, one solver after the other (each with its default kernel)
+    solvers = []
+    for k, c in enumerate(cavs):
+        xi = pkg.islbm_mesh_tanh(c["n"], 1.5)
+        s = pkg.Solver(xi, xi, Ra=c["Ra"], precision="fp32")
+        s.set_fields(temperature_noise(s.shape, 1e-6, seed=k))
+        s.step(128)
+        solvers.append(s)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in solvers:
+        s.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    for s in solvers:
+        s.close()
+    print(json.dumps({"batch": True, "cavities": len(cavs), "nodes": nodes, "steps": K,
+                      "MLUPS_batched": nodes * K / (t_batch * 1e6),
+                      "MLUPS_sequential": nodes * K / (t_seq * 1e6),
+                      "speedup": t_seq / t_batch, "tile_rows_used": rows,
+                      "setup_s_with_autotune": t_setup,
+                      "GBps_batched": 112 * nodes * K / t_batch / 1e9}), flush=True)
+
+
+def cavities_sorted(cavs):
+    return sorted(cavs, key=lambda c: c["n"])
+
+
 def sweep3d(args, pkg, torch, flush):
     """The 3-D step (D3Q19 + D3Q7) on the 256^3 tanh mesh and the uniform mesh."""
     n = 256
@@ -351,6 +409,9 @@ def main():
         return
     if args.sweep3d:
         sweep3d(args, pkg, torch, flush)
+        return
+    if args.batch:
+        batch(args, pkg, torch)
         return
     solver = make_solver(pkg, n, args.mesh, args.Ra, args.precision, args.kernel)
     info = solver.info

@@ -260,6 +260,56 @@ ISLBM_API islbm_status islbm_synchronize(islbm_t h);
 ISLBM_API islbm_status islbm_save(islbm_t h, const char* path);
 ISLBM_API islbm_status islbm_load(islbm_t h, const char* path);
 
+/* ---- batched cavities (a sweep of independent problems) ----------------------
+ * A batch advances many 2-D cavities of different sizes and Rayleigh numbers
+ * together: one persistent kernel launch per step (per tile height) walks a
+ * work list of (cavity, tile) items over all of them, and blocks of steps are
+ * replayed from CUDA graphs.  Each cavity is an ordinary solver handle owned
+ * by the batch (islbm_batch_member): set its fields, read its fields and
+ * reductions through the single-cavity entry points, but advance it only with
+ * islbm_batch_step. */
+typedef enum { ISLBM_MESH_UNIFORM = 0, ISLBM_MESH_ERF = 1, ISLBM_MESH_TANH = 2 } islbm_mesh_kind;
+typedef struct {
+  int n;          /* fluid nodes per axis (square cavity)           */
+  int mesh;       /* islbm_mesh_kind                                 */
+  double a;       /* stretching parameter (erf / tanh)               */
+  double Ra, Pr;
+} islbm_cavity;
+typedef struct islbm_batch* islbm_batch_t;
+
+/* Time the step-kernel variants (islbm_params.kernel 1..6) of one square mesh
+ * with CUDA events on `stream` (30 steps after 5 warm-up steps each) and
+ * return the fastest in *best; us_per_step (host, may be NULL) receives
+ * ISLBM_KERNEL_VARIANTS entries (+inf for variants that cannot run).  Results
+ * are cached per (n, mesh, a, precision) for the life of the process.
+ * FP32 / FP16DEV / BF16DEV only. */
+#define ISLBM_KERNEL_VARIANTS 7
+ISLBM_API islbm_status islbm_autotune(int n, int mesh, double a, int precision, void* stream,
+                                      int* best, double* us_per_step);
+
+/* Create a batch of `count` cavities (host array, copied) with one storage
+ * precision (FP32 / FP16DEV / BF16DEV).  opt: common parameters (NULL =
+ * defaults).  autotune != 0 chooses each mesh size's tile height with
+ * islbm_autotune; otherwise 8-row tiles.  stream: shared by all members. */
+ISLBM_API islbm_status islbm_batch_create(int count, const islbm_cavity* cavities, int precision,
+                                          const islbm_params* opt, int autotune, void* stream,
+                                          islbm_batch_t* out);
+ISLBM_API void islbm_batch_destroy(islbm_batch_t b);
+/* The solver handle of cavity i (owned by the batch). */
+ISLBM_API islbm_status islbm_batch_member(islbm_batch_t b, int i, islbm_t* out);
+/* Tile height (rows) used for cavity i: 8 or 16 (0 for a bad index). */
+ISLBM_API int islbm_batch_tile_rows(islbm_batch_t b, int i);
+/* Advance every cavity by n steps (asynchronous). */
+ISLBM_API islbm_status islbm_batch_step(islbm_batch_t b, long long n);
+/* Wait for the batch; reports a timeout of a bounded wait as ISLBM_ERR_TIMEOUT. */
+ISLBM_API islbm_status islbm_batch_synchronize(islbm_batch_t b);
+/* Step in blocks of `interval` until every cavity meets the steady criterion of
+ * Sec. 3 (islbm_steady_change below tol) or max_steps have been taken;
+ * steps_to_steady (host, count entries, may be NULL) receives each cavity's
+ * step count at which it first met it (-1: not reached). */
+ISLBM_API islbm_status islbm_batch_run_to_steady(islbm_batch_t b, double tol, long long interval,
+                                                 long long max_steps, long long* steps_to_steady);
+
 /* ---- reductions without allocation ------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers of
  * this library that cannot allocate device memory: code that runs while its

@@ -3,7 +3,7 @@
 The compute path is the CUDA library libislbm.so (sm_103a); this package is
 its Python binding.  See include/islbm.h for the C ABI.
 """
-from .islbm import (EXPORTS, KERNELS, LATTICES, PRECISIONS, STENCILS, IslbmError, Params, Solver,
+from .islbm import (EXPORTS, KERNELS, LATTICES, MESH_KINDS, Batch, islbm_autotune, PRECISIONS, STENCILS, IslbmError, Params, Solver,
                     islbm_create, islbm_default_params, islbm_destroy, islbm_get_fields,
                     islbm_get_fields_device, islbm_get_populations, islbm_info, islbm_load,
                     islbm_mass, islbm_mesh_erf, islbm_mesh_tanh, islbm_mesh_uniform,

@@ -14,7 +14,9 @@
 // stored after the collision instead of before it.
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "islbm_internal.h"
 #include "islbm_store.cuh"
@@ -820,6 +822,88 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Batched persistent step: many cavities of different sizes in one launch.
+// The work list holds (cavity, tile) items; each cavity brings its own
+// parameters, output buffers and TMA descriptors (in global memory).
+// ---------------------------------------------------------------------------
+
+template <typename S>
+struct alignas(128) BatchCav {
+  CUtensorMap map[2];      // descriptors of the cavity's two buffers
+  P2<float> p;
+  S* out[2];               // output buffer when reading buffer 0 / 1
+};
+
+template <typename S, int R, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_step_tma_batch(const BatchCav<S>* __restrict__ cavs, const int2* __restrict__ items,
+                     int nitems, int parity, unsigned step, int* err) {
+  using G = TileGeom<S, R>;
+  constexpr int TY = G::TY, HX = G::HX;
+  constexpr unsigned BUF = (unsigned)(14 * G::PLANE * sizeof(S));
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)STAGES * BUF);
+  auto origin = [&](const P2<float>& p, int t, int& x0, int& y0, int& ry0) {
+    const int ntx = (p.nx + kTX - 1) / kTX;
+    const int ty = t / ntx;
+    x0 = (t - ty * ntx) * kTX;
+    y0 = ty * TY;
+    ry0 = max(0, min(y0 - 1, p.ny - 3));
+  };
+  auto issue = [&](int item, int st) {
+    const int2 it = items[item];
+    const BatchCav<S>& cv = cavs[it.x];
+    int x0, y0, ry0;
+    origin(cv.p, it.y, x0, y0, ry0);
+    mbar_expect_tx(&bars[st], BUF);
+    tma_load_3d(smem_raw + (size_t)st * BUF, &cv.map[parity], x0 - HX, ry0, 0, &bars[st]);
+  };
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < STAGES; ++st) mbar_init(&bars[st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int st = 0; st < STAGES; ++st) {
+      const int i = blockIdx.x + st * gridDim.x;
+      if (i < nitems) issue(i, st);
+    }
+  for (int k = 0;; ++k) {
+    const int i = blockIdx.x + k * gridDim.x;
+    if (i >= nitems) break;
+    const int st = k % STAGES;
+    const bool ok = mbar_wait(&bars[st], (unsigned)(k / STAGES) & 1u);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        for (int j = 0; j < STAGES; ++j) {
+          const int kk = k + j;
+          if (blockIdx.x + kk * gridDim.x < nitems)
+            mbar_wait(&bars[kk % STAGES], (unsigned)(kk / STAGES) & 1u);
+        }
+      }
+      return;
+    }
+    const int2 it = items[i];
+    const BatchCav<S>& cv = cavs[it.x];
+    P2<float> p = cv.p;
+    p.step = step;
+    int x0, y0, ry0;
+    origin(p, it.y, x0, y0, ry0);
+    const S* sm = reinterpret_cast<const S*>(smem_raw + (size_t)st * BUF);
+    tile_body<S, R, false>(sm, p.py[0] + y0, p.py[1] + y0, x0, y0, ry0, cv.out[parity], p);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int in = i + STAGES * gridDim.x;
+      if (in < nitems) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        issue(in, st);
+      }
+    }
+  }
+}
+
 template <typename S, int R, bool UNI>
 cudaError_t launch_tiled(const Solver& s, const S* in, S* out, const P2<float>& p) {
   using G = TileGeom<S, R>;
@@ -1012,6 +1096,90 @@ cudaError_t launch_steady(Solver& s) {
 cudaError_t launch_finish_reduce(Solver& s) {
   k_finish<<<1, 32 * RED_COUNT, 0, s.stream>>>(s.dscratch, s.red_blocks, s.dresult);
   return cudaGetLastError();
+}
+
+// ---- batched step ----
+namespace {
+
+template <typename S, int R>
+struct BatchGroupImpl : BatchGroup {
+  BatchCav<S>* dcavs = nullptr;
+  int2* ditems = nullptr;
+  int ncav = 0, nitems = 0, grid = 0;
+  size_t smem = 0;
+  ~BatchGroupImpl() override {
+    if (dcavs) cudaFree(dcavs);
+    if (ditems) cudaFree(ditems);
+  }
+  cudaError_t launch(cudaStream_t st, int parity, unsigned step, int* err) override {
+    k_step_tma_batch<S, R, 2><<<grid, kThreads, smem, st>>>(dcavs, ditems, nitems, parity, step,
+                                                           err);
+    return cudaGetLastError();
+  }
+};
+
+template <typename S, int R>
+cudaError_t make_group_impl(const std::vector<Solver*>& members, int sm_count,
+                            cudaStream_t stream, BatchGroup** out) {
+  using G = TileGeom<S, R>;
+  auto* g = new BatchGroupImpl<S, R>();
+  g->smem = (size_t)2 * 14 * G::PLANE * sizeof(S) + 64;
+  cudaError_t e = cudaFuncSetAttribute(k_step_tma_batch<S, R, 2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem);
+  int bps = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_step_tma_batch<S, R, 2>, kThreads,
+                                                      g->smem);
+  std::vector<BatchCav<S>> cavs(members.size());
+  std::vector<int2> items;
+  for (size_t c = 0; c < members.size() && e == cudaSuccess; ++c) {
+    Solver& m = *members[c];
+    std::memcpy(&cavs[c].map[0], m.tmap[0], sizeof(CUtensorMap));
+    std::memcpy(&cavs[c].map[1], m.tmap[1], sizeof(CUtensorMap));
+    cavs[c].p = make_params<float>(m);
+    cavs[c].out[0] = static_cast<S*>(m.buf[1]);
+    cavs[c].out[1] = static_cast<S*>(m.buf[0]);
+    const int ntiles = ((m.n[0] + kTX - 1) / kTX) * ((m.n[1] + G::TY - 1) / G::TY);
+    for (int t = 0; t < ntiles; ++t) items.push_back(make_int2((int)c, t));
+  }
+  g->ncav = (int)members.size();
+  g->nitems = (int)items.size();
+  g->grid = std::max(1, std::min(g->nitems, sm_count * std::max(bps, 1)));
+  if (e == cudaSuccess) e = cudaMalloc(&g->dcavs, cavs.size() * sizeof(BatchCav<S>));
+  if (e == cudaSuccess) e = cudaMalloc(&g->ditems, items.size() * sizeof(int2));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->dcavs, cavs.data(), cavs.size() * sizeof(BatchCav<S>),
+                        cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->ditems, items.data(), items.size() * sizeof(int2),
+                        cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    delete g;
+    return e;
+  }
+  *out = g;
+  return cudaSuccess;
+}
+
+template <int R>
+cudaError_t make_group_r(const std::vector<Solver*>& m, int precision, int sm, cudaStream_t st,
+                         BatchGroup** out) {
+  switch (precision) {
+    case ISLBM_FP32: return make_group_impl<float, R>(m, sm, st, out);
+    case ISLBM_FP16DEV: return make_group_impl<__half, R>(m, sm, st, out);
+    case ISLBM_BF16DEV: return make_group_impl<__nv_bfloat16, R>(m, sm, st, out);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t make_batch_group(const std::vector<Solver*>& members, int tile_rows, int precision,
+                             int sm_count, cudaStream_t stream, BatchGroup** out) {
+  if (tile_rows == 2) return make_group_r<2>(members, precision, sm_count, stream, out);
+  if (tile_rows == 4) return make_group_r<4>(members, precision, sm_count, stream, out);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace islbm

@@ -148,5 +148,16 @@ cudaError_t launch_steady_3d(Solver& s);
 
 }  // namespace islbm
 
+namespace islbm {
+// One launch configuration of the batched step: the cavities sharing a tile
+// height, with their device-side parameter records and work list.
+struct BatchGroup {
+  virtual ~BatchGroup() {}
+  virtual cudaError_t launch(cudaStream_t stream, int parity, unsigned step, int* err) = 0;
+};
+cudaError_t make_batch_group(const std::vector<Solver*>& members, int tile_rows, int precision,
+                             int sm_count, cudaStream_t stream, BatchGroup** out);
+}  // namespace islbm
+
 // The opaque handle of the C ABI is the solver itself.
 struct islbm_solver : public islbm::Solver {};

@@ -32,7 +32,11 @@ EXPORTS = (
     "islbm_get_fields", "islbm_get_fields_device", "islbm_get_populations", "islbm_reduce",
     "islbm_nusselt", "islbm_reynolds", "islbm_mass", "islbm_synchronize", "islbm_save",
     "islbm_load", "islbm_reduce_noalloc", "islbm_steady_change", "islbm_run_to_steady",
+    "islbm_autotune", "islbm_batch_create", "islbm_batch_destroy", "islbm_batch_member",
+    "islbm_batch_tile_rows", "islbm_batch_step", "islbm_batch_synchronize",
+    "islbm_batch_run_to_steady",
 )
+MESH_KINDS = {"uniform": 0, "erf": 1, "tanh": 2}
 
 
 class IslbmError(RuntimeError):
@@ -64,6 +68,11 @@ class Reductions(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
                 ("Nu", "Nu_hot", "Nu_cold", "Nu_middle", "Re", "Re_uv", "Re_mean", "mass", "ke",
                  "max_speed", "nonfinite")] + [("time", ctypes.c_longlong)]
+
+
+class Cavity(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("mesh", ctypes.c_int), ("a", ctypes.c_double),
+                ("Ra", ctypes.c_double), ("Pr", ctypes.c_double)]
 
 
 class NuOut(ctypes.Structure):
@@ -118,6 +127,15 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
         "islbm_load": (i, [h, ctypes.c_char_p]),
         "islbm_reduce_noalloc": (i, [vp, vp, i, i, vp, vp, d, d, P(Params), vp, P(Reductions)]),
         "islbm_steady_change": (i, [h, dp, dp]),
+        "islbm_autotune": (i, [i, i, d, i, vp, P(i), dp]),
+        "islbm_batch_create": (i, [i, P(Cavity), i, P(Params), i, vp, P(h)]),
+        "islbm_batch_destroy": (None, [h]),
+        "islbm_batch_member": (i, [h, i, P(h)]),
+        "islbm_batch_tile_rows": (i, [h, i]),
+        "islbm_batch_step": (i, [h, ctypes.c_longlong]),
+        "islbm_batch_synchronize": (i, [h]),
+        "islbm_batch_run_to_steady": (i, [h, d, ctypes.c_longlong, ctypes.c_longlong,
+                                          P(ctypes.c_longlong)]),
         "islbm_run_to_steady": (i, [h, d, ctypes.c_longlong, ctypes.c_longlong,
                                     P(ctypes.c_longlong), dp, dp]),
     }
@@ -341,6 +359,81 @@ def islbm_reduce_noalloc(f, g, nx, ny, xi_x, xi_y, Ra, Pr=0.71, params: Params |
     return {k: getattr(r, k) for k, _ in Reductions._fields_}
 
 
+def islbm_autotune(n, mesh="tanh", a=1.5, precision="fp32", stream=None):
+    """Fastest step-kernel variant of a square mesh and the per-variant step times (us)."""
+    best = ctypes.c_int()
+    us = (ctypes.c_double * 7)()
+    if stream is None:
+        stream = _current_stream()
+    _check(load_library().islbm_autotune(int(n), MESH_KINDS[mesh], float(a), PRECISIONS[precision],
+                                         stream, ctypes.byref(best), us))
+    return best.value, list(us)
+
+
+class _Member(object):
+    """A batch member: the single-cavity calls on a handle owned by the batch."""
+
+
+class Batch:
+    """Many cavities advanced together (islbm_batch_*)."""
+
+    def __init__(self, cavities, precision="fp32", autotune=False, params: Params | None = None,
+                 stream=None):
+        arr = (Cavity * len(cavities))()
+        for k, c in enumerate(cavities):
+            arr[k] = Cavity(int(c["n"]), MESH_KINDS[c.get("mesh", "tanh")], float(c.get("a", 1.5)),
+                            float(c["Ra"]), float(c.get("Pr", 0.71)))
+        h = ctypes.c_void_p()
+        if stream is None:
+            stream = _current_stream()
+        _check(load_library().islbm_batch_create(len(cavities), arr, PRECISIONS[precision],
+                                                 ctypes.byref(params) if params is not None else None,
+                                                 1 if autotune else 0, stream, ctypes.byref(h)))
+        self.h = h
+        self.count = len(cavities)
+        self.members = []
+        for k in range(self.count):
+            m = ctypes.c_void_p()
+            _check(load_library().islbm_batch_member(self.h, k, ctypes.byref(m)))
+            s = Solver.__new__(Solver)
+            s.h = m
+            s.owned = False
+            s.info = islbm_info(m)
+            s.dim = 2
+            s.shape = (s.info.n[1], s.info.n[0])
+            self.members.append(s)
+
+    def tile_rows(self, k):
+        return load_library().islbm_batch_tile_rows(self.h, k)
+
+    def step(self, n=1):
+        _check(load_library().islbm_batch_step(self.h, int(n)))
+
+    def synchronize(self):
+        _check(load_library().islbm_batch_synchronize(self.h))
+
+    def run_to_steady(self, tol=1e-9, interval=2000, max_steps=10_000_000, check=True):
+        steps = (ctypes.c_longlong * self.count)()
+        st = load_library().islbm_batch_run_to_steady(self.h, float(tol), int(interval),
+                                                      int(max_steps), steps)
+        if check:
+            _check(st)
+        return list(steps), st
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in self.members:
+                m.h = None
+            load_library().islbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------------------
 # convenience wrapper
 # ---------------------------------------------------------------------------
@@ -363,9 +456,9 @@ class Solver:
         self.shape = (n[1], n[0]) if self.dim == 2 else (n[2], n[1], n[0])
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "owned", True):
             islbm_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
