@@ -310,6 +310,88 @@ ISLBM_API islbm_status islbm_batch_synchronize(islbm_batch_t b);
 ISLBM_API islbm_status islbm_batch_run_to_steady(islbm_batch_t b, double tol, long long interval,
                                                  long long max_steps, long long* steps_to_steady);
 
+/* Steady-Nu criterion for flows that settle to a statistically steady state
+ * (a persistent oscillation on a coarse mesh never meets the field criterion
+ * above): every `sample` steps each cavity's volume-averaged Nu and Re
+ * (islbm_reduce) are recorded; after every `window` samples their window
+ * means are formed, and a cavity is steady at the end of the first window
+ * whose mean Nu differs from the previous window's by at most tol * |mean|.
+ * steps_to_steady, nu_mean, re_mean (host, count entries each, may be NULL)
+ * receive the step count (-1: not reached) and the window means of that
+ * window (of the last window for a cavity that did not converge).  Steps
+ * continue in whole samples until every cavity is steady or the next sample
+ * would pass max_steps (then ISLBM_ERR_NOT_CONVERGED).  ISLBM_ERR_ARG for
+ * tol <= 0, sample <= 0 or window < 2.  Not in the paper, whose runs are
+ * converged with the field criterion. */
+ISLBM_API islbm_status islbm_batch_run_to_steady_nu(islbm_batch_t b, double tol, long long sample,
+                                                    int window, long long max_steps,
+                                                    long long* steps_to_steady, double* nu_mean,
+                                                    double* re_mean);
+
+/* ---- warm-start network kernels ----------------------------------------------
+ * Not part of the paper's method: these kernels train and evaluate a small
+ * convolutional network that predicts the steady cavity state from
+ * (log Ra, Pr, stretching) so that islbm_set_fields can start the solver near
+ * it.  All pointers are device pointers; every call is asynchronous on
+ * `stream`, returns ISLBM_ERR_ARG for NULL pointers or bad sizes (nothing
+ * launched) and ISLBM_ERR_CUDA if the launch fails.  Tensors are NHWC, FP32
+ * unless stated; "bf16" buffers hold __nv_bfloat16. */
+/* C[M,N] (+)= op(A) op(B) (+ bias[N]) on the tensor cores (mma.sync BF16, FP32
+ * accumulation).  transA = 0: A is M x K row-major with leading dimension lda;
+ * 1: A is K x M row-major.  transB = 0: B is K x N row-major; 1: N x K.
+ * accumulate != 0 adds to C.  A, B: bf16; C, bias: FP32 (bias may be NULL).
+ * When the output tiles are too few to fill the GPU the K range is split
+ * over blocks that add their parts with FP32 atomics (summation order then
+ * varies from run to run).  ISLBM_ERR_ARG also for ldc < N or a leading
+ * dimension of A or B shorter than its row. */
+ISLBM_API islbm_status islbm_cnn_gemm_bf16(const void* A, const void* B, float* C,
+                                           const float* bias, int M, int N, int K, int lda,
+                                           int ldb, int ldc, int transA, int transB,
+                                           int accumulate, void* stream);
+/* 3x3 zero-padded im2col of in[B,H,W,C] into bf16 rows col[B*H*W][kpad]
+ * ordered [dy][dx][c]; kpad >= 9C, the extra columns are zero. */
+ISLBM_API islbm_status islbm_cnn_im2col(const float* in, void* col, int B, int H, int W, int C,
+                                        int kpad, void* stream);
+/* Adjoint of islbm_cnn_im2col: din[B,H,W,C] from dcol[B*H*W][kpad] (written, not added). */
+ISLBM_API islbm_status islbm_cnn_col2im(const float* dcol, float* din, int B, int H, int W,
+                                        int C, int kpad, void* stream);
+/* Nearest-neighbour 2x upsampling of in[B,H,W,C] into out[B,2H,2W,C]; with
+ * backward != 0 the adjoint: in is the gradient [B,2H,2W,C], out [B,H,W,C]. */
+ISLBM_API islbm_status islbm_cnn_upsample2x(const float* in, float* out, int B, int H, int W,
+                                            int C, int backward, void* stream);
+/* x = tanh(x) in place; and dy *= 1 - y^2 (y = tanh output). */
+ISLBM_API islbm_status islbm_cnn_tanh(float* x, long long n, void* stream);
+ISLBM_API islbm_status islbm_cnn_tanh_back(const float* y, float* dy, long long n, void* stream);
+/* FP32 -> bf16 copy of n values. */
+ISLBM_API islbm_status islbm_cnn_to_bf16(const float* x, void* y, long long n, void* stream);
+/* out[N] (+)= column sums of the M x N row-major x (chunks of rows are added
+ * with FP32 atomics; the order varies). */
+ISLBM_API islbm_status islbm_cnn_colsum(const float* x, float* out, int M, int N, int accumulate,
+                                        void* stream);
+/* Weighted mean squared error of y against t (n values, channel weights wc of
+ * period C, NULL = 1): dy = 2 wc (y - t) / n, and `blocks` partial sums of
+ * wc (y - t)^2 in partial[blocks] (FP64; their sum / n is the loss). */
+ISLBM_API islbm_status islbm_cnn_mse(const float* y, const float* t, const float* wc, int C,
+                                     float* dy, double* partial, int blocks, long long n,
+                                     void* stream);
+/* One Adam step (Kingma & Ba) of n FP32 weights w with gradient g and moments
+ * m, v at step t >= 1; wb (may be NULL) receives the bf16 copy of w. */
+ISLBM_API islbm_status islbm_cnn_adam(float* w, void* wb, const float* g, float* m, float* v,
+                                      long long n, float lr, float beta1, float beta2,
+                                      float eps, long long t, void* stream);
+
+/* Solver fields <-> network channels for `nodes` nodes (the 2-D node order of
+ * islbm_get_fields_device): y[3k..3k+2] = ((T - T_mid) / T_scale,
+ * u / u_scale, v / u_scale) with T, u, v FP64 device arrays and y FP32 NHWC;
+ * unpack is the inverse.  ISLBM_ERR_ARG for NULL pointers, nodes <= 0 or a
+ * zero scale (pack). */
+ISLBM_API islbm_status islbm_cnn_pack_fields(const double* T, const double* u, const double* v,
+                                             long long nodes, double T_mid, double T_scale,
+                                             double u_scale, float* y, void* stream);
+ISLBM_API islbm_status islbm_cnn_unpack_fields(const float* y, long long nodes, double T_mid,
+                                               double T_scale, double u_scale, double* T,
+                                               double* u, double* v, void* stream);
+
 /* ---- reductions without allocation ------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers of
  * this library that cannot allocate device memory: code that runs while its

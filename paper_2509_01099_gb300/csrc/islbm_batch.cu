@@ -335,3 +335,54 @@ extern "C" islbm_status islbm_batch_run_to_steady(islbm_batch_t b, double tol, l
   return left == 0 ? ISLBM_OK
                    : bfail(b, ISLBM_ERR_NOT_CONVERGED, "islbm_batch_run_to_steady: step budget exhausted");
 }
+
+extern "C" islbm_status islbm_batch_run_to_steady_nu(islbm_batch_t b, double tol, long long sample,
+                                                     int window, long long max_steps,
+                                                     long long* steps_to_steady, double* nu_mean,
+                                                     double* re_mean) {
+  if (!b || !(tol > 0) || sample <= 0 || window < 2 || max_steps < 0)
+    return bfail(b, ISLBM_ERR_ARG,
+                 "islbm_batch_run_to_steady_nu: tol > 0, sample > 0, window >= 2");
+  const size_t n = b->members.size();
+  std::vector<long long> done(n, -1);
+  std::vector<double> sum_nu(n, 0.0), sum_re(n, 0.0), prev(n, NAN), nu_out(n, NAN), re_out(n, NAN);
+  long long t = 0;
+  int in_window = 0;
+  size_t left = n;
+  while (left > 0 && t + sample <= max_steps) {
+    islbm_status st = islbm_batch_step(b, sample);
+    if (st == ISLBM_OK) st = islbm_batch_synchronize(b);
+    if (st != ISLBM_OK) return st;
+    t += sample;
+    for (size_t i = 0; i < n; ++i) {
+      islbm_reductions r;
+      st = islbm_reduce(b->members[i], &r);
+      if (st != ISLBM_OK) return bfail(b, st, member_error(b->members[i]));
+      sum_nu[i] += r.Nu;
+      sum_re[i] += r.Re;
+    }
+    if (++in_window < window) continue;
+    in_window = 0;
+    for (size_t i = 0; i < n; ++i) {
+      const double m = sum_nu[i] / window, mr = sum_re[i] / window;
+      sum_nu[i] = sum_re[i] = 0.0;
+      if (done[i] < 0) {
+        nu_out[i] = m;
+        re_out[i] = mr;
+        if (std::isfinite(prev[i]) && std::fabs(m - prev[i]) <= tol * std::fabs(m)) {
+          done[i] = t;
+          --left;
+        }
+      }
+      prev[i] = m;
+    }
+  }
+  for (size_t i = 0; i < n; ++i) {
+    if (steps_to_steady) steps_to_steady[i] = done[i];
+    if (nu_mean) nu_mean[i] = nu_out[i];
+    if (re_mean) re_mean[i] = re_out[i];
+  }
+  return left == 0 ? ISLBM_OK
+                   : bfail(b, ISLBM_ERR_NOT_CONVERGED,
+                           "islbm_batch_run_to_steady_nu: step budget exhausted");
+}

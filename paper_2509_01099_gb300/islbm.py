@@ -34,7 +34,10 @@ EXPORTS = (
     "islbm_load", "islbm_reduce_noalloc", "islbm_steady_change", "islbm_run_to_steady",
     "islbm_autotune", "islbm_batch_create", "islbm_batch_destroy", "islbm_batch_member",
     "islbm_batch_tile_rows", "islbm_batch_step", "islbm_batch_synchronize",
-    "islbm_batch_run_to_steady",
+    "islbm_batch_run_to_steady", "islbm_batch_run_to_steady_nu", "islbm_cnn_gemm_bf16", "islbm_cnn_im2col", "islbm_cnn_col2im",
+    "islbm_cnn_upsample2x", "islbm_cnn_tanh", "islbm_cnn_tanh_back", "islbm_cnn_to_bf16",
+    "islbm_cnn_colsum", "islbm_cnn_mse", "islbm_cnn_adam", "islbm_cnn_pack_fields",
+    "islbm_cnn_unpack_fields",
 )
 MESH_KINDS = {"uniform": 0, "erf": 1, "tanh": 2}
 
@@ -134,8 +137,24 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
         "islbm_batch_tile_rows": (i, [h, i]),
         "islbm_batch_step": (i, [h, ctypes.c_longlong]),
         "islbm_batch_synchronize": (i, [h]),
+        "islbm_batch_run_to_steady_nu": (i, [h, d, ctypes.c_longlong, i, ctypes.c_longlong,
+                                             P(ctypes.c_longlong), dp, dp]),
         "islbm_batch_run_to_steady": (i, [h, d, ctypes.c_longlong, ctypes.c_longlong,
                                           P(ctypes.c_longlong)]),
+        "islbm_cnn_gemm_bf16": (i, [vp, vp, vp, vp, i, i, i, i, i, i, i, i, i, vp]),
+        "islbm_cnn_im2col": (i, [vp, vp, i, i, i, i, i, vp]),
+        "islbm_cnn_col2im": (i, [vp, vp, i, i, i, i, i, vp]),
+        "islbm_cnn_upsample2x": (i, [vp, vp, i, i, i, i, i, vp]),
+        "islbm_cnn_tanh": (i, [vp, ctypes.c_longlong, vp]),
+        "islbm_cnn_tanh_back": (i, [vp, vp, ctypes.c_longlong, vp]),
+        "islbm_cnn_to_bf16": (i, [vp, vp, ctypes.c_longlong, vp]),
+        "islbm_cnn_colsum": (i, [vp, vp, i, i, i, vp]),
+        "islbm_cnn_mse": (i, [vp, vp, vp, i, vp, vp, i, ctypes.c_longlong, vp]),
+        "islbm_cnn_pack_fields": (i, [vp, vp, vp, ctypes.c_longlong, d, d, d, vp, vp]),
+        "islbm_cnn_unpack_fields": (i, [vp, ctypes.c_longlong, d, d, d, vp, vp, vp, vp]),
+        "islbm_cnn_adam": (i, [vp, vp, vp, vp, vp, ctypes.c_longlong, ctypes.c_float,
+                               ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_longlong, vp]),
         "islbm_run_to_steady": (i, [h, d, ctypes.c_longlong, ctypes.c_longlong,
                                     P(ctypes.c_longlong), dp, dp]),
     }
@@ -419,6 +438,19 @@ class Batch:
         if check:
             _check(st)
         return list(steps), st
+
+    def run_to_steady_nu(self, tol=1e-3, sample=1000, window=100, max_steps=10_000_000,
+                         check=True):
+        """islbm_batch_run_to_steady_nu: (steps, nu_mean, re_mean, status)."""
+        steps = (ctypes.c_longlong * self.count)()
+        nu = (ctypes.c_double * self.count)()
+        re = (ctypes.c_double * self.count)()
+        st = load_library().islbm_batch_run_to_steady_nu(self.h, float(tol), int(sample),
+                                                         int(window), int(max_steps), steps, nu,
+                                                         re)
+        if check:
+            _check(st)
+        return list(steps), list(nu), list(re), st
 
     def close(self):
         if getattr(self, "h", None):

@@ -10,7 +10,8 @@ Generators:
     generators", OOPSLA 2014): a counter-based stream, so element k of a draw
     depends only on (seed, k).  Used for the initial temperature noise of the
     cavity runs and for random population states.
-  * numpy's PCG64 for the Ra / mesh-size draws of the batched sweep.
+  * numpy's PCG64 for the Ra / mesh-size draws of the batched sweep and the
+    Gaussian weights of the warm-start network tests.
 """
 from __future__ import annotations
 
@@ -92,3 +93,13 @@ def ra_sweep(count: int, seed: int = 0, log10_lo: float = 6.0, log10_hi: float =
     ra = 10.0 ** rng.uniform(log10_lo, log10_hi, size=count)
     n = rng.choice(np.asarray(sizes), size=count)
     return ra, n
+
+
+def gaussian_arrays(shapes, seed: int, scales=None) -> dict:
+    """Independent N(0, scale^2) float64 arrays, one per (name, shape) pair, in order.
+
+    Used for the weights and inputs of the warm-start network's parity tests;
+    scales maps a name to its standard deviation (default 1)."""
+    rng = np.random.default_rng(seed)
+    scales = scales or {}
+    return {name: rng.standard_normal(shape) * scales.get(name, 1.0) for name, shape in shapes}

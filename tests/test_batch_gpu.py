@@ -81,3 +81,32 @@ def test_autotuned_sweep_batch_runs_to_steady():
         r = m.reduce()
         assert 1.0 < r["Nu"] < 3.0
     b.close()
+
+
+def test_batch_steady_nu_criterion():
+    """Window means of Nu: the reported step count is a whole number of windows,
+    the reported mean agrees with the Nu the field criterion converges to, and
+    the arguments are validated."""
+    cavs = [dict(n=32, mesh="tanh", Ra=1e4), dict(n=40, mesh="tanh", Ra=3e4)]
+    b = pkg.Batch(cavs, precision="fp32")
+    with pytest.raises(pkg.IslbmError):
+        b.run_to_steady_nu(tol=0.0)
+    with pytest.raises(pkg.IslbmError):
+        b.run_to_steady_nu(window=1)
+    steps, nu, re, st = b.run_to_steady_nu(tol=1e-4, sample=200, window=20, max_steps=400_000)
+    assert st == 0
+    for s in steps:
+        assert s > 0 and s % (200 * 20) == 0
+    ref = pkg.Batch(cavs, precision="fp32")
+    ref.run_to_steady(tol=1e-7, interval=1000, max_steps=600_000)
+    for k, m in enumerate(ref.members):
+        r = m.reduce()
+        assert abs(nu[k] - r["Nu"]) < 2e-3 * r["Nu"]
+        assert abs(re[k] - r["Re"]) < 5e-3 * r["Re"]
+    # a budget shorter than two windows cannot converge
+    c = pkg.Batch(cavs, precision="fp32")
+    steps, nu, re, st = c.run_to_steady_nu(tol=1e-4, sample=100, window=10, max_steps=1500,
+                                           check=False)
+    assert st == 5 and steps == [-1, -1]      # ISLBM_ERR_NOT_CONVERGED
+    for x in (b, ref, c):
+        x.close()
