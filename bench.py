@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--dim", type=int, default=2, choices=[2, 3],
+                    help="2: n x n cavity (D2Q9 + D2Q5); 3: n^3 cavity (D3Q19 + D3Q7)")
     ap.add_argument("--Ra", type=float, default=1e8)
     ap.add_argument("--mesh", default="tanh", choices=["tanh", "erf", "uniform"])
     ap.add_argument("--precision", default="fp32", choices=list(BYTES_PER_VALUE))
@@ -51,7 +53,7 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="time every kernel variant and storage type; print one JSON line each")
     ap.add_argument("--steady", action="store_true",
-                    help="wall time to the steady state per storage type (256^2 tanh mesh)")
+                    help="wall time to a steady Nu: plain, mixed precision, learned warm start")
     ap.add_argument("--sweep3d", action="store_true", help="time the 3-D step (256^3)")
     ap.add_argument("--batch", action="store_true",
                     help="64-cavity Ra sweep: batched persistent launch vs a per-cavity loop")
@@ -65,22 +67,36 @@ def peaks():
         return None
 
 
-def profile_traffic():
-    """ncu DRAM bytes per launch of the step kernel, if the committed summary was
-    taken from the current kernel source (else None)."""
+KERNEL_SOURCES = {
+    2: ("islbm_d2.cu", "islbm_store.cuh", "islbm_tma.cuh"),
+    3: ("islbm_d3_tma.cu", "islbm_d3_common.cuh", "islbm_store.cuh", "islbm_tma.cuh"),
+}
+
+
+def kernel_source_sha(dim):
+    """sha256 over the step kernel's source files (in the order of KERNEL_SOURCES)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "step2d_fp32_tanh1024.md")
-    src = os.path.join(ROOT, "paper_2509_01099_gb300", "csrc", "islbm_d2.cu")
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[dim]:
+        with open(os.path.join(ROOT, "paper_2509_01099_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profile_traffic(dim, precision, mesh, n):
+    """ncu DRAM bytes per launch of the step kernel from the committed summary
+    profiles/step{dim}d_{precision}_{mesh}{n}.md, if it was taken from the current
+    kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"step{dim}d_{precision}_{mesh}{n}.md")
     try:
         text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         vals = {}
         for line in text.splitlines():
             line = line.strip().lstrip("-").strip()
             if line.startswith(("traffic_bytes_per_launch:", "source_sha256:")):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.split()[0].strip("`")
-        if vals.get("source_sha256") == sha:
+        if vals.get("source_sha256") == kernel_source_sha(dim):
             return float(vals["traffic_bytes_per_launch"])
     except Exception:
         pass
@@ -222,10 +238,17 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def make_solver(pkg, n, mesh, Ra, precision, kernel="auto"):
+def make_solver(pkg, n, mesh, Ra, precision, kernel="auto", dim=2):
     """A solver built entirely by the library (its own mesh helpers)."""
     xi = pkg.islbm_mesh_uniform(n) if mesh == "uniform" else getattr(pkg, "islbm_mesh_" + mesh)(n, 1.5)
-    return pkg.Solver(xi, xi, Ra=Ra, precision=precision, kernel=kernel)
+    return pkg.Solver(*([xi] * dim), Ra=Ra, precision=precision, kernel=kernel)
+
+
+KERNEL_NAMES = {1: "k_step / k_step3 (direct: one thread per node, interpolation through L1)",
+                2: "k_step_tiled (cp.async tile staging)",
+                3: "k_step_tma<S,4,2>", 4: "k_step_tma<S,2,2>", 5: "k_step_tma<S,2,3>",
+                6: "k_step_tma<S,4,3>",
+                7: "k_step3_tma (3-D: warp-specialised TMA ring of population pairs)"}
 
 
 def sweep(args, pkg, torch, flush):
@@ -249,31 +272,36 @@ def sweep(args, pkg, torch, flush):
                     s.close()
 
 
+WARMSTART_WEIGHTS = os.path.join(ROOT, "paper_2509_01099_gb300", "weights", "warmstart_tanh256.npz")
+
+
 def steady(args, pkg, torch):
-    """Wall time until the steady criterion of Sec. 3 holds, per storage type, on
-    the 256^2 tanh-stretched cavity (a = 1.5) at Ra = 1e7, from rest; the
-    criterion is 1e-7 for FP32 and 1e-5 for the 16-bit forms over 2000 steps."""
-    from synthetic import temperature_noise
-    n, Ra = 256, 1e7
-    out = {}
-    for prec, tol in (("fp32", 1e-7), ("fp16dev", 1e-5), ("bf16dev", 1e-5)):
-        s = make_solver(pkg, n, "tanh", Ra, prec)
-        s.set_fields(temperature_noise(s.shape, 1e-6, seed=0))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r = s.run_to_steady(tol=tol, interval=2000, max_steps=4_000_000, check=False)
-        red = s.reduce(check=False)
-        wall = time.perf_counter() - t0
-        out[prec] = {"steps": r["steps"], "wall_s": wall, "converged": r["status"] == 0,
-                     "du": r["du"], "dT": r["dT"], "Nu": red["Nu"], "Nu_hot": red["Nu_hot"],
-                     "Re": red["Re"], "tf": r["steps"] / s.info.steps_per_tf,
-                     "MLUPS": n * n * r["steps"] / (wall * 1e6)}
-        s.close()
-    for prec in ("fp16dev", "bf16dev"):
-        out[prec]["Nu_rel_to_fp32"] = out[prec]["Nu"] / out["fp32"]["Nu"] - 1
-        out[prec]["wall_rel_to_fp32"] = out[prec]["wall_s"] / out["fp32"]["wall_s"]
-    print(json.dumps({"steady": True, "workload": f"2-D cavity {n}^2 tanh a=1.5, Ra={Ra:g}",
-                      "results": out}), flush=True)
+    """Wall time to a steady Nu on the 256^2 tanh-stretched cavity (a = 1.5) for
+    16 held-out Ra log-uniform in [1e6, 1e8] (PCG64 seed 2): plain (FP32 from
+    rest), mixed (FP16 / BF16 deviation storage from rest) and learned (FP32 and
+    FP16 started from the warm-start network's prediction).  Each arm is one
+    batch of the 16 cavities run until every window mean of Nu (100 samples
+    1000 steps apart) changes by at most 2e-4 (islbm_batch_run_to_steady_nu)."""
+    from paper_2509_01099_gb300 import warmstart as ws
+    from synthetic import ra_sweep
+    ras = ra_sweep(16, seed=2)[0]
+    net = ws.load(WARMSTART_WEIGHTS)
+    arms = (("fp32", "rest"), ("fp16dev", "rest"), ("bf16dev", "rest"), ("fp32", "warm"),
+            ("fp16dev", "warm"))
+    res = ws.compare(net, ras, arms=arms)
+    plain = res["fp32/rest"]
+    summary = {}
+    for key, arm in res.items():
+        nu_dev = [abs(a / b - 1) for a, b in zip(arm["Nu"], plain["Nu"])]
+        re_dev = [abs(a / b - 1) for a, b in zip(arm["Re"], plain["Re"])]
+        summary[key] = {"wall_s": arm["wall_s"], "steps_total": int(sum(arm["steps"])),
+                        "steps_max": int(max(arm["steps"])), "converged": arm["status"] == 0,
+                        "wall_rel_to_plain": arm["wall_s"] / plain["wall_s"],
+                        "max_Nu_dev_from_plain": max(nu_dev), "max_Re_dev_from_plain": max(re_dev)}
+    print(json.dumps({"steady": True, "workload": "2-D cavity 256^2 tanh a=1.5, 16 held-out Ra "
+                      "in [1e6, 1e8] (seed 2)", "criterion": "Nu window means, 100 x 1000 steps, "
+                      "tol 2e-4", "Ra": [float(r) for r in ras], "summary": summary,
+                      "arms": res}), flush=True)
 
 
 def batch(args, pkg, torch):
@@ -333,21 +361,23 @@ def cavities_sorted(cavs):
 
 
 def sweep3d(args, pkg, torch, flush):
-    """The 3-D step (D3Q19 + D3Q7) on the 256^3 tanh mesh and the uniform mesh."""
+    """The 3-D step (D3Q19 + D3Q7) on the 256^3 tanh mesh and the uniform mesh,
+    with the direct kernel and the pipelined TMA kernel."""
     n = 256
     for mesh in ("tanh", "uniform"):
-        for prec in ("fp32", "bf16dev"):
-            xi = pkg.islbm_mesh_uniform(n) if mesh == "uniform" else pkg.islbm_mesh_tanh(n, 1.5)
-            s = pkg.Solver(xi, xi, xi, Ra=1e7, precision=prec)
-            steps = 20
-            t = timed_steps(pkg, s, steps, 3, flush, torch)
-            nodes = n ** 3
-            b = 2 * 26 * BYTES_PER_VALUE[prec]
-            print(json.dumps({"sweep3d": True, "n": n, "mesh": mesh, "precision": prec,
-                              "kernel": s.info.kernel, "MLUPS": nodes * steps / (t * 1e6),
-                              "GBps": b * nodes / (t / steps) / 1e9,
-                              "us_per_step": 1e6 * t / steps}), flush=True)
-            s.close()
+        for prec in ("fp32", "fp16dev", "bf16dev"):
+            for kernel in ("direct", "tma3d"):
+                xi = pkg.islbm_mesh_uniform(n) if mesh == "uniform" else pkg.islbm_mesh_tanh(n, 1.5)
+                s = pkg.Solver(xi, xi, xi, Ra=1e7, precision=prec, kernel=kernel)
+                steps = 20
+                t = timed_steps(pkg, s, steps, 3, flush, torch)
+                nodes = n ** 3
+                b = 2 * 26 * BYTES_PER_VALUE[prec]
+                print(json.dumps({"sweep3d": True, "n": n, "mesh": mesh, "precision": prec,
+                                  "kernel": s.info.kernel, "MLUPS": nodes * steps / (t * 1e6),
+                                  "GBps": b * nodes / (t / steps) / 1e9,
+                                  "us_per_step": 1e6 * t / steps}), flush=True)
+                s.close()
 
 
 def flush_l2(flush):
@@ -398,7 +428,8 @@ def main():
     from synthetic import temperature_noise
 
     n = args.n
-    nodes = n * n
+    dim = args.dim
+    nodes = n ** dim
     flush = [torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda"),
              torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")]
     if args.sweep:
@@ -413,7 +444,7 @@ def main():
     if args.batch:
         batch(args, pkg, torch)
         return
-    solver = make_solver(pkg, n, args.mesh, args.Ra, args.precision, args.kernel)
+    solver = make_solver(pkg, n, args.mesh, args.Ra, args.precision, args.kernel, dim)
     info = solver.info
 
     clocks = ClockSampler(local)
@@ -437,24 +468,27 @@ def main():
     inner = 100
     pin = lambda: torch.empty(nodes, dtype=torch.float64, pin_memory=True).numpy()
     hT, hu, hv = pin(), pin(), pin()
-    hT[:] = temperature_noise((n, n), 1e-6, seed=0).ravel()
+    hw = pin() if dim == 3 else None
+    hT[:] = temperature_noise(solver.shape, 1e-6, seed=0).ravel()
     hu[:] = 0.0
     hv[:] = 0.0
+    if hw is not None:
+        hw[:] = 0.0
     e2e_iters = max(3, min(20, args.steps // inner))
-    solver.set_fields(hT, hu, hv)
+    solver.set_fields(hT, hu, hv, hw)
     solver.step(inner)
     solver.reduce(check=False)
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_iters):
-        solver.set_fields(hT, hu, hv)        # H2D of the step's inputs (pinned)
+        solver.set_fields(hT, hu, hv, hw)    # H2D of the step's inputs (pinned)
         solver.step(inner)
         solver.reduce(check=False)           # D2H of the result (Nu, Re, mass, ...)
     t_e2e = max_over_ranks(world, time.perf_counter() - t0)
     e2e_value = world * nodes * inner * e2e_iters / (t_e2e * 1e6)
 
     variants = {}
-    if not args.no_variants:
+    if not args.no_variants and dim == 2:
         for mesh, prec in (("uniform", "fp32"), ("tanh", "fp16dev"), ("uniform", "fp16dev"),
                            ("tanh", "bf16dev")):
             s2 = make_solver(pkg, n, mesh, args.Ra, prec)
@@ -473,8 +507,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": WORKLOAD if (n == 1024 and args.mesh == "tanh") else
-                       f"2-D cavity {n}x{n} {args.mesh}, Ra={args.Ra:g}",
+            "config": {"workload": WORKLOAD if (n == 1024 and args.mesh == "tanh" and dim == 2) else
+                       (f"2-D cavity {n}x{n} {args.mesh}, Ra={args.Ra:g}" if dim == 2 else
+                        f"3-D cavity {n}^3 {args.mesh}, D3Q19+D3Q7, Ra={args.Ra:g}"),
                        "n": n, "mesh": args.mesh, "a": 1.5, "Ra": args.Ra, "Pr": 0.71,
                        "precision": args.precision, "parallelism": f"replicas{world}",
                        "l2": "before every timed step: 256 MB write, then 256 MB read of another buffer (cold, clean L2)",
@@ -482,18 +517,18 @@ def main():
             "wctpdt_s": ms_per_step * 1e-3 * info.steps_per_tf,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src,
-                         "traffic": profile_traffic(),
+                         "traffic": profile_traffic(dim, args.precision, args.mesh, n),
                          "bytes_per_update": bytes_per_update,
-                         "kernel": "k_step_tma<float,2,2> (fused pull+interpolate+walls+collide, TMA-pipelined)"},
+                         "kernel": KERNEL_NAMES.get(info.kernel, str(info.kernel))},
             "e2e": {"value": e2e_value, "unit": "MLUPS",
-                    "h2d_bytes_per_step": 3 * 8 * nodes, "d2h_bytes_per_step": 8 * 16,
+                    "h2d_bytes_per_step": (dim + 1) * 8 * nodes, "d2h_bytes_per_step": 8 * 16,
                     "definition": f"per step: set_fields from pinned host T,u,v + {inner} time steps + reduce read back"},
             "gpu_launches": args.steps,
             "clocks": clk,
             "state_check": {"Nu": red.get("Nu"), "Re": red.get("Re"), "status": red.get("status")},
             "variants": variants,
         }
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and dim == 2:
             line["cpu_baseline"] = cpu_baseline(n, 6, args.mesh)
         print(json.dumps(line), flush=True)
     solver.close()

@@ -88,12 +88,16 @@ typedef struct {
   double s_e, s_eps, s_q, s_pi, s_m;   /* flow MRT rates (Sec. 2.1)            */
   double q_j, q_e, q_nu;               /* temperature MRT rates (Sec. 2.1)     */
   int stencil;        /* islbm_stencil                                          */
-  int kernel;         /* step-kernel variant of the 2-D FP32/16-bit path: 0 = chosen
-                         by the library; 1 direct (one thread per node); 2 tiled
-                         (cp.async tile staging); 3-6 persistent TMA pipelines
-                         (64x16 / 64x8 tiles, 2 / 3 stages: 3 = 16 rows 2 stages,
-                         4 = 8 rows 2 stages, 5 = 8 rows 3 stages, 6 = 16 rows
-                         3 stages).  Ignored for FP64, 3-D and the upwind stencil. */
+  int kernel;         /* step-kernel variant of the FP32/16-bit paths: 0 = chosen
+                         by the library; 1 direct (one thread per node); 2-D:
+                         2 tiled (cp.async tile staging); 3-6 persistent TMA
+                         pipelines (64x16 / 64x8 tiles, 2 / 3 stages: 3 = 16
+                         rows 2 stages, 4 = 8 rows 2 stages, 5 = 8 rows 3
+                         stages, 6 = 16 rows 3 stages); 3-D: 7 persistent TMA
+                         ring of opposite-population pairs (32x4x2 tiles, needs
+                         n_y >= 6, n_z >= 4).  2-6 in 3-D and every variant for
+                         FP64 or the upwind stencil run the direct kernel; 7 in
+                         2-D is ISLBM_ERR_ARG. */
   int reference;      /* reference temperature T0 of the buoyancy force and of T*
                          (Sec. 2.1): ISLBM_TREF_COLD = the cold wall (default;
                          reproduces the asymmetric centre values of Table 3),
@@ -277,13 +281,13 @@ typedef struct {
 } islbm_cavity;
 typedef struct islbm_batch* islbm_batch_t;
 
-/* Time the step-kernel variants (islbm_params.kernel 1..6) of one square mesh
+/* Time the 2-D step-kernel variants (islbm_params.kernel 1..6) of one square mesh
  * with CUDA events on `stream` (30 steps after 5 warm-up steps each) and
  * return the fastest in *best; us_per_step (host, may be NULL) receives
  * ISLBM_KERNEL_VARIANTS entries (+inf for variants that cannot run).  Results
  * are cached per (n, mesh, a, precision) for the life of the process.
  * FP32 / FP16DEV / BF16DEV only. */
-#define ISLBM_KERNEL_VARIANTS 7
+#define ISLBM_KERNEL_VARIANTS 8
 ISLBM_API islbm_status islbm_autotune(int n, int mesh, double a, int precision, void* stream,
                                       int* best, double* us_per_step);
 

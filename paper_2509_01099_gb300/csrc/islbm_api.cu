@@ -138,6 +138,26 @@ std::string encode_tensor_maps(Solver* s) {
                                      ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                      : (s->precision == ISLBM_FP16DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  if (s->dim == 3) {
+    // 4-D view [population][z][y][x] of a buffer; one box holds a tile + halo of two planes
+    unsigned b4[4];
+    step_3d_tma_box((int)s->elem, b4);
+    const cuuint64_t dims[4] = {(cuuint64_t)s->pitch, (cuuint64_t)s->n[1], (cuuint64_t)s->n[2],
+                                (cuuint64_t)(s->qf + s->qg)};
+    const cuuint64_t strides[3] = {(cuuint64_t)s->pitch * s->elem,
+                                   (cuuint64_t)s->pitch * s->n[1] * s->elem,
+                                   (cuuint64_t)s->plane * s->elem};
+    const cuuint32_t box[4] = {b4[0], b4[1], b4[2], b4[3]};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int b = 0; b < 2; ++b) {
+      CUresult r = reinterpret_cast<EncodeFn>(fn)(
+          reinterpret_cast<CUtensorMap*>(s->tmap[b]), dt, 4, s->buf[b], dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    }
+    return "";
+  }
   const cuuint64_t dims[3] = {(cuuint64_t)s->pitch, (cuuint64_t)s->n[1], 14};
   const cuuint64_t strides[2] = {(cuuint64_t)s->pitch * s->elem, (cuuint64_t)s->plane * s->elem};
   const cuuint32_t box[3] = {(cuuint32_t)(64 + 2 * hx), (cuuint32_t)(4 * R + 2), 14};
@@ -282,7 +302,7 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
   if (!(prm.Ma > 0)) return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: Ma must be positive");
   if (prm.stencil != ISLBM_STENCIL_CENTRED && prm.stencil != ISLBM_STENCIL_UPWIND)
     return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: unknown stencil");
-  if (prm.kernel < 0 || prm.kernel >= KV_COUNT)
+  if (prm.kernel < 0 || prm.kernel >= KV_COUNT || (dim == 2 && prm.kernel == KV_TMA_3D))
     return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: unknown kernel variant");
   const double* xis[3] = {xi_x, xi_y, xi_z};
   const int ns[3] = {nx, ny, dim == 3 ? nz : 1};
@@ -390,13 +410,18 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
   cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
   // step-kernel variant: the pipelined TMA kernel for stretched 2-D meshes in
   // FP32 / 16-bit storage, the direct kernel otherwise
+  // (and the 3-D pipelined kernel for stretched 3-D meshes)
   if (prm.kernel != KV_AUTO)
     s->variant = prm.kernel;
-  else
-    s->variant = (dim == 2 && precision != ISLBM_FP64 && !s->uniform)
+  else if (dim == 2)
+    s->variant = (precision != ISLBM_FP64 && !s->uniform)
                      ? (precision == ISLBM_FP32 ? KV_TMA_R2S2 : KV_TMA_R4S2)
                      : KV_DIRECT;
-  if (dim == 3 || precision == ISLBM_FP64 || prm.stencil != ISLBM_STENCIL_CENTRED)
+  else
+    s->variant = s->uniform ? KV_DIRECT : KV_TMA_3D;
+  if (precision == ISLBM_FP64 || prm.stencil != ISLBM_STENCIL_CENTRED)
+    s->variant = KV_DIRECT;
+  if (dim == 3 && (s->variant != KV_TMA_3D || s->n[1] < 6 || s->n[2] < 4))
     s->variant = KV_DIRECT;
   s->elem = precision == ISLBM_FP64 ? 8 : (precision == ISLBM_FP32 ? 4 : 2);
   s->pitch = (s->n[0] + 31) / 32 * 32;

@@ -32,7 +32,7 @@ enum RedSlot {
 
 constexpr int RED_STRIDE = 16;   // doubles per block partial (>= RED_COUNT)
 
-// Step-kernel variants of the 2-D FP32/16-bit path (islbm_params.kernel).
+// Step-kernel variants of the FP32/16-bit paths (islbm_params.kernel).
 enum KernelVariant {
   KV_AUTO = 0,      // chosen by the library (islbm_create)
   KV_DIRECT = 1,    // one thread per node, interpolation from global memory
@@ -41,6 +41,7 @@ enum KernelVariant {
   KV_TMA_R2S2 = 4,  // persistent, TMA double buffer, 64 x 8 tiles
   KV_TMA_R2S3 = 5,  // persistent, TMA triple buffer, 64 x 8 tiles
   KV_TMA_R4S3 = 6,  // persistent, TMA triple buffer, 64 x 16 tiles
+  KV_TMA_3D = 7,    // 3-D: persistent, warp-specialised TMA ring of population pairs
   KV_COUNT
 };
 
@@ -135,6 +136,9 @@ cudaError_t launch_init_fields_3d(Solver& s, const double* rho, const double* T,
                                   const double* u0, const double* u1, const double* u2);
 cudaError_t launch_init_populations_3d(Solver& s, const double* f, const double* g);
 cudaError_t launch_step_3d(Solver& s);
+cudaError_t launch_step_3d_tma(Solver& s);
+// TMA box (x, y, z, planes) of the 3-D pipelined kernel; returns its bytes
+size_t step_3d_tma_box(int elem, unsigned (&box)[4]);
 cudaError_t launch_fields_3d(Solver& s, double* rho, double* T, double* u0, double* u1,
                              double* u2);
 cudaError_t launch_populations_3d(Solver& s, double* f, double* g);

@@ -19,8 +19,9 @@ LATTICES = {"d2q9_d2q5": 0, "d3q19_d3q7": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16dev": 2, "bf16dev": 3}
 STENCILS = {"centred": 0, "upwind": 1}
 REFERENCES = {"mean": 0, "cold": 1}
+KERNEL_VARIANTS = 8      # ISLBM_KERNEL_VARIANTS of include/islbm.h
 KERNELS = {"auto": 0, "direct": 1, "tiled": 2, "tma_r4s2": 3, "tma_r2s2": 4, "tma_r2s3": 5,
-           "tma_r4s3": 6}
+           "tma_r4s3": 6, "tma3d": 7}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_DIVERGED",
           5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_IO"}
 
@@ -381,7 +382,7 @@ def islbm_reduce_noalloc(f, g, nx, ny, xi_x, xi_y, Ra, Pr=0.71, params: Params |
 def islbm_autotune(n, mesh="tanh", a=1.5, precision="fp32", stream=None):
     """Fastest step-kernel variant of a square mesh and the per-variant step times (us)."""
     best = ctypes.c_int()
-    us = (ctypes.c_double * 7)()
+    us = (ctypes.c_double * KERNEL_VARIANTS)()
     if stream is None:
         stream = _current_stream()
     _check(load_library().islbm_autotune(int(n), MESH_KINDS[mesh], float(a), PRECISIONS[precision],

@@ -74,8 +74,6 @@ def snapshot_dataset(ras, steps, snapshots=20, every=50_000, n=DEFAULT_N, a=DEFA
     feats = np.repeat(features(np.log10(ras), [pr] * len(ras), [a] * len(ras)), snapshots, axis=0)
     log = {"first": first, "every": every, "steps": steps, "wall_s": 0.0, "du": []}
     t0 = time.perf_counter()
-    for m in batch.members:
-        m.steady_change()
     batch.step(first)
     for j in range(snapshots):
         if j:
@@ -90,8 +88,10 @@ def snapshot_dataset(ras, steps, snapshots=20, every=50_000, n=DEFAULT_N, a=DEFA
                                           ctypes.c_void_p(buf.v.data_ptr()), nodes, T_mid,
                                           T_scale, u_scale, ctypes.c_void_p(dst.data_ptr()),
                                           _stream()))
-            if j == snapshots - 1:
-                row.append(m.steady_change()[0])
+            if j >= snapshots - 2:
+                du = m.steady_change()[0]   # change between the last two snapshots
+                if j == snapshots - 1:
+                    row.append(du)
         if row:
             log["du"] = row
     batch.synchronize()
@@ -138,24 +138,25 @@ def warm_start(net: WarmStartNet, solver, Ra, Pr=0.71, a=DEFAULT_A, buf=None):
     return buf
 
 
-def compare(net: WarmStartNet, ras, tol=2e-3, sample=1000, window=100, max_steps=4_000_000,
-            n=DEFAULT_N, a=DEFAULT_A, pr=0.71, precision="fp32"):
-    """From-rest and warm-started runs of the same cavities to a steady Nu.
+def compare(net: WarmStartNet, ras, tol=2e-4, sample=1000, window=100, max_steps=4_000_000,
+            n=DEFAULT_N, a=DEFAULT_A, pr=0.71, arms=(("fp32", "rest"), ("fp32", "warm"))):
+    """Runs of the same cavities to a steady Nu, one batch per arm.
 
-    The criterion is islbm_batch_run_to_steady_nu (window means of the
-    volume-averaged Nu, `window` samples `sample` steps apart, agreeing to
-    `tol`): on a 256^2 mesh the flow above Ra ~ 3e7 keeps a small oscillation
-    and never meets the field criterion.  Each arm is one batch of all
-    cavities; its wall time runs from just after the batch is created (the
-    warm arm includes the network's inference and the equilibrium
-    initialisation) until every cavity is steady."""
+    An arm is (storage precision, start): "rest" is the rest state, "warm" the
+    network's prediction.  The criterion is islbm_batch_run_to_steady_nu
+    (window means of the volume-averaged Nu, `window` samples `sample` steps
+    apart, agreeing to `tol`): on a 256^2 mesh the flow above Ra ~ 3e7 keeps a
+    small oscillation and never meets the field criterion.  An arm's wall time
+    runs from just after its batch is created (for "warm" it includes the
+    network's inference and the equilibrium initialisation) until every cavity
+    is steady.  The warm arms also report Nu / Re of the predicted state."""
     import torch
     out = {}
-    for arm in ("rest", "warm"):
+    for precision, start in arms:
         batch = Batch(cavities(ras, n, a, pr), precision)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        if arm == "warm":
+        if start == "warm":
             buf = _FieldBuffers(n * n)
             for m, r in zip(batch.members, ras):
                 warm_start(net, m, r, pr, a, buf)
@@ -163,9 +164,20 @@ def compare(net: WarmStartNet, ras, tol=2e-3, sample=1000, window=100, max_steps
         steps, nu, re, st = batch.run_to_steady_nu(tol, sample, window, max_steps, check=False)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        out[arm] = {"steps": list(steps), "status": int(st), "wall_s": wall, "Nu": list(nu),
-                    "Re": list(re)}
+        arm = {"precision": precision, "start": start, "steps": list(steps), "status": int(st),
+               "wall_s": wall, "Nu": list(nu), "Re": list(re)}
         batch.close()
+        if start == "warm":
+            probe = Batch(cavities(ras, n, a, pr), precision)
+            buf = _FieldBuffers(n * n)
+            red0 = []
+            for m, r in zip(probe.members, ras):
+                warm_start(net, m, r, pr, a, buf)
+                red0.append(m.reduce())
+            arm["Nu_pred"] = [x["Nu"] for x in red0]
+            arm["Re_pred"] = [x["Re"] for x in red0]
+            probe.close()
+        out[f"{precision}/{start}"] = arm
     return out
 
 
@@ -227,7 +239,7 @@ def main(argv=None):
     tr.add_argument("--snapshots", type=int, default=20)
     tr.add_argument("--steps", type=int, default=2_000_000)
     tr.add_argument("--every", type=int, default=50_000)
-    tr.add_argument("--iters", type=int, default=4000)
+    tr.add_argument("--iters", type=int, default=16000)
     tr.add_argument("--batch", type=int, default=16)
     tr.add_argument("--lr", type=float, default=2e-3)
     tr.add_argument("--log10-lo", type=float, default=6.0)
@@ -235,10 +247,12 @@ def main(argv=None):
     ev = sub.add_parser("compare")
     ev.add_argument("--weights", required=True)
     ev.add_argument("--held", type=int, default=16)
-    ev.add_argument("--tol", type=float, default=2e-3)
+    ev.add_argument("--tol", type=float, default=2e-4)
     ev.add_argument("--sample", type=int, default=1000)
     ev.add_argument("--window", type=int, default=100)
     ev.add_argument("--max-steps", type=int, default=4_000_000)
+    ev.add_argument("--arms", default="fp32/rest,fp32/warm",
+                    help="comma-separated precision/start pairs (start: rest or warm)")
     ev.add_argument("--log10-lo", type=float, default=6.0)
     ev.add_argument("--log10-hi", type=float, default=8.0)
     args = ap.parse_args(argv)
@@ -257,13 +271,15 @@ def main(argv=None):
                 "every": args.every, "iters": args.iters, "batch": args.batch,
                 "train_s": time.perf_counter() - t0, "loss_first": losses[0][1],
                 "loss_last": losses[-1][1], "params": net.n_params,
+                "loss_curve": [[int(i), float(v)] for i, v in losses[::10]],
                 "log10_ra": [args.log10_lo, args.log10_hi]}
         save(net, args.out, meta)
         print(json.dumps(meta), flush=True)
     else:
         net = load(args.weights)
         ras = ra_sweep(args.held, seed=2, log10_lo=args.log10_lo, log10_hi=args.log10_hi)[0]
-        res = compare(net, ras, args.tol, args.sample, args.window, args.max_steps)
+        arms = [tuple(x.split("/")) for x in args.arms.split(",")]
+        res = compare(net, ras, args.tol, args.sample, args.window, args.max_steps, arms=arms)
         res["Ra"] = [float(r) for r in ras]
         print(json.dumps(res), flush=True)
 

@@ -91,3 +91,13 @@ def test_diffusivity_range_is_checked(lib):
     with pytest.raises(pkg.IslbmError) as e:
         _create(xi, xi, Ra=1e-4)
     assert e.value.status == 1
+
+
+def test_kernel_variant_count_matches_header():
+    import re
+    from pathlib import Path
+    from paper_2509_01099_gb300 import islbm as B
+    text = (Path(__file__).resolve().parents[1] / "include" / "islbm.h").read_text()
+    n = int(re.search(r"#define ISLBM_KERNEL_VARIANTS (\d+)", text).group(1))
+    assert B.KERNEL_VARIANTS == n
+    assert sorted(B.KERNELS.values()) == list(range(n))

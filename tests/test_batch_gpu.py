@@ -98,7 +98,7 @@ def test_batch_steady_nu_criterion():
     for s in steps:
         assert s > 0 and s % (200 * 20) == 0
     ref = pkg.Batch(cavs, precision="fp32")
-    ref.run_to_steady(tol=1e-7, interval=1000, max_steps=600_000)
+    ref.run_to_steady(tol=1e-6, interval=1000, max_steps=600_000)
     for k, m in enumerate(ref.members):
         r = m.reduce()
         assert abs(nu[k] - r["Nu"]) < 2e-3 * r["Nu"]

@@ -88,3 +88,84 @@ def test_random_state_populations_3d(mesh, precision, steps):
     s.close()
     assert np.abs(fp - fp_ref).max() / np.abs(fp_ref).max() <= POP_TOL[precision]
     assert np.abs(gp - gp_ref).max() / np.abs(gp_ref).max() <= POP_TOL[precision]
+
+
+MESHES["erf36"] = lambda: (O.mesh_erf(36, 1.5),) * 3
+
+
+@pytest.mark.parametrize("kernel", ["direct", "tma3d"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
+def test_step_kernels_3d_random_state(kernel, precision):
+    """Both 3-D step kernels on a mesh of several tiles in every direction
+    (36 = 32 + a ragged 4 in x) from a far-from-equilibrium state."""
+    xi = MESHES["erf36"]()
+    cav = O.Cavity(*xi, params=O.Params(Ra=1e6))
+    f = random_populations(19, cav.shape, seed=31, spread=0.2)
+    g = random_signed(7, cav.shape, seed=32, amplitude=0.08)
+    cav.init_populations(f, g)
+    cav.step(3)
+    fp_ref, gp_ref = cav.post_collision()
+    s = pkg.Solver(*xi, Ra=1e6, precision=precision, kernel=kernel)
+    assert s.info.kernel == pkg.KERNELS[kernel]
+    s.set_populations(f, g)
+    s.step(3)
+    fp, gp = s.populations()
+    s.close()
+    assert np.abs(fp - fp_ref).max() / np.abs(fp_ref).max() <= POP_TOL[precision]
+    assert np.abs(gp - gp_ref).max() / np.abs(gp_ref).max() <= POP_TOL[precision]
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_erf36(steps):
+    return oracle_run("erf36", 1e6, steps)
+
+
+def test_tma3d_cavity_fields_multi_tile():
+    steps = 300
+    ref = oracle_erf36(steps)
+    xi = MESHES["erf36"]()
+    s = pkg.Solver(*xi, Ra=1e6, precision="fp32")
+    assert s.info.kernel == pkg.KERNELS["tma3d"]      # the default for stretched 3-D meshes
+    s.set_fields(temperature_noise(s.shape, 1e-6, seed=0))
+    s.step(steps)
+    got = s.fields()
+    red = s.reduce()
+    s.close()
+    assert rel_field_error(got["T"], ref["T"]) <= TOL["fp32"]
+    assert rel_vector_error([got[k] for k in "uvw"], [ref[k] for k in "uvw"]) <= TOL["fp32"]
+    for k in ("Nu", "Nu_hot", "Nu_cold", "Re"):
+        assert abs(red[k] - ref["red"][k]) / max(1.0, abs(ref["red"][k])) <= NU_TOL["fp32"]
+
+
+def test_tma3d_matches_direct_kernel_closely():
+    """The two kernels apply the same operations in the same order; after 200
+    steps their fields agree far inside the oracle tolerance."""
+    xi = MESHES["erf36"]()
+    out = {}
+    for kernel in ("direct", "tma3d"):
+        s = pkg.Solver(*xi, Ra=1e7, precision="fp32", kernel=kernel)
+        s.set_fields(temperature_noise(s.shape, 1e-6, seed=3))
+        s.step(200)
+        out[kernel] = s.fields()
+        s.close()
+    for k in ("T", "u", "v", "w"):
+        a, b = out["direct"][k], out["tma3d"][k]
+        assert np.abs(a - b).max() <= 1e-6 * max(np.abs(b).max(), 1e-30), k
+
+
+def test_3d_kernel_default_choice():
+    xi = O.mesh_tanh(16, 1.5)
+    cases = [((xi,) * 3, "fp32", "tma3d"), ((xi,) * 3, "bf16dev", "tma3d"),
+             ((xi,) * 3, "fp64", "direct"), (MESHES["uniform11x9x7"](), "fp32", "direct")]
+    for mesh, precision, kernel in cases:
+        s = pkg.Solver(*mesh, Ra=1e6, precision=precision)
+        assert s.info.kernel == pkg.KERNELS[kernel], (precision, kernel)
+        s.close()
+    # too few nodes across for the staged window: the direct kernel
+    small = O.mesh_tanh(5, 1.5)
+    s = pkg.Solver(small, small, small, Ra=1e6, precision="fp32", kernel="tma3d")
+    assert s.info.kernel == pkg.KERNELS["direct"]
+    s.close()
+    # the 3-D kernel on a 2-D mesh is an argument error
+    with pytest.raises(pkg.IslbmError):
+        pkg.Solver(xi, xi, Ra=1e6, precision="fp32", kernel="tma3d")
