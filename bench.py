@@ -85,21 +85,31 @@ def kernel_source_sha(dim):
 
 def profile_traffic(dim, precision, mesh, n):
     """ncu DRAM bytes per launch of the step kernel from the committed summary
-    profiles/step{dim}d_{precision}_{mesh}{n}.md, if it was taken from the current
-    kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"step{dim}d_{precision}_{mesh}{n}.md")
-    try:
-        text = open(path).read()
-        vals = {}
-        for line in text.splitlines():
-            line = line.strip().lstrip("-").strip()
-            if line.startswith(("traffic_bytes_per_launch:", "source_sha256:")):
-                k, v = line.split(":", 1)
-                vals[k.strip()] = v.split()[0].strip("`")
-        if vals.get("source_sha256") == kernel_source_sha(dim):
-            return float(vals["traffic_bytes_per_launch"])
-    except Exception:
-        pass
+    profiles/step{dim}d_{precision}_{mesh}{m}.md taken from the current kernel
+    source (else None).  A summary of another size m is scaled by the node
+    count (every node's populations are read and written once per step)."""
+    import glob
+    paths = sorted(glob.glob(os.path.join(ROOT, "profiles", f"step{dim}d_{precision}_{mesh}*.md")))
+    exact = os.path.join(ROOT, "profiles", f"step{dim}d_{precision}_{mesh}{n}.md")
+    if exact in paths:
+        paths = [exact]
+    for path in paths:
+        try:
+            text = open(path).read()
+            vals = {}
+            for line in text.splitlines():
+                line = line.strip().lstrip("-").strip()
+                if line.startswith(("traffic_bytes_per_launch:", "source_sha256:",
+                                    "nodes_per_launch:")):
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.split()[0].strip("`")
+            if vals.get("source_sha256") != kernel_source_sha(dim):
+                continue
+            traffic = float(vals["traffic_bytes_per_launch"])
+            nodes = float(vals.get("nodes_per_launch", n ** dim))
+            return traffic * (n ** dim) / nodes
+        except Exception:
+            continue
     return None
 
 

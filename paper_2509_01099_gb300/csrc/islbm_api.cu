@@ -139,23 +139,26 @@ std::string encode_tensor_maps(Solver* s) {
                                      : (s->precision == ISLBM_FP16DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
   if (s->dim == 3) {
-    // 4-D view [population][z][y][x] of a buffer; one box holds a tile + halo of two planes
-    unsigned b4[4];
-    step_3d_tma_box((int)s->elem, b4);
+    // 4-D view [population][z][y][x] of a buffer; a box holds a tile of two planes
+    // with a halo along the axes in the bits of its type (1 x, 2 y, 4 z)
     const cuuint64_t dims[4] = {(cuuint64_t)s->pitch, (cuuint64_t)s->n[1], (cuuint64_t)s->n[2],
                                 (cuuint64_t)(s->qf + s->qg)};
     const cuuint64_t strides[3] = {(cuuint64_t)s->pitch * s->elem,
                                    (cuuint64_t)s->pitch * s->n[1] * s->elem,
                                    (cuuint64_t)s->plane * s->elem};
-    const cuuint32_t box[4] = {b4[0], b4[1], b4[2], b4[3]};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    for (int b = 0; b < 2; ++b) {
-      CUresult r = reinterpret_cast<EncodeFn>(fn)(
-          reinterpret_cast<CUtensorMap*>(s->tmap[b]), dt, 4, s->buf[b], dims, strides, box, estr,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
-    }
+    for (int b = 0; b < 2; ++b)
+      for (int type = 0; type < 7; ++type) {
+        unsigned b4[4];
+        step_3d_tma_box((int)s->elem, type, b4);
+        const cuuint32_t box[4] = {b4[0], b4[1], b4[2], b4[3]};
+        CUresult r = reinterpret_cast<EncodeFn>(fn)(
+            reinterpret_cast<CUtensorMap*>(s->tmap3[b][type]), dt, 4, s->buf[b], dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+          return "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+      }
     return "";
   }
   const cuuint64_t dims[3] = {(cuuint64_t)s->pitch, (cuuint64_t)s->n[1], 14};
@@ -421,7 +424,7 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
     s->variant = s->uniform ? KV_DIRECT : KV_TMA_3D;
   if (precision == ISLBM_FP64 || prm.stencil != ISLBM_STENCIL_CENTRED)
     s->variant = KV_DIRECT;
-  if (dim == 3 && (s->variant != KV_TMA_3D || s->n[1] < 6 || s->n[2] < 4))
+  if (dim == 3 && (s->variant != KV_TMA_3D || !step_3d_tma_fits(s->n[1], s->n[2])))
     s->variant = KV_DIRECT;
   s->elem = precision == ISLBM_FP64 ? 8 : (precision == ISLBM_FP32 ? 4 : 2);
   s->pitch = (s->n[0] + 31) / 32 * 32;

@@ -106,6 +106,7 @@ struct Solver {
   int sm_count = 0;
   int* derr = nullptr;            // device error flag of the pipelined kernels
   alignas(128) unsigned char tmap[2][128];   // TMA descriptors of buf[0] / buf[1]
+  alignas(128) unsigned char tmap3[2][7][128];   // 3-D: one descriptor per box shape
   // CUDA graphs of kGraphSteps steps, one per starting buffer, replayed on a
   // private stream that is ordered against `stream` with events
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -137,8 +138,11 @@ cudaError_t launch_init_fields_3d(Solver& s, const double* rho, const double* T,
 cudaError_t launch_init_populations_3d(Solver& s, const double* f, const double* g);
 cudaError_t launch_step_3d(Solver& s);
 cudaError_t launch_step_3d_tma(Solver& s);
-// TMA box (x, y, z, planes) of the 3-D pipelined kernel; returns its bytes
-size_t step_3d_tma_box(int elem, unsigned (&box)[4]);
+// TMA box (x, y, z, planes) of the 3-D pipelined kernel for a pair moving along
+// the axes in the bits of `type` (1 x, 2 y, 4 z)
+void step_3d_tma_box(int elem, int type, unsigned (&box)[4]);
+// whether the 3-D pipelined kernel's staged window fits the mesh
+bool step_3d_tma_fits(int ny, int nz);
 cudaError_t launch_fields_3d(Solver& s, double* rho, double* T, double* u0, double* u1,
                              double* u2);
 cudaError_t launch_populations_3d(Solver& s, double* f, double* g);
