@@ -55,6 +55,12 @@ def parse():
     ap.add_argument("--steady", action="store_true",
                     help="wall time to a steady Nu: plain, mixed precision, learned warm start")
     ap.add_argument("--sweep3d", action="store_true", help="time the 3-D step (256^3)")
+    ap.add_argument("--convergence", action="store_true",
+                    help="Ra=1e6 grid convergence on 257/513/1025 erf meshes (Table 2)")
+    ap.add_argument("--max-steps", type=int, default=0, help="step budget of --convergence")
+    ap.add_argument("--series", action="store_true",
+                    help="1024^2 Ra=1e8 for --series-steps steps with Nu every 1000 steps")
+    ap.add_argument("--series-steps", type=int, default=200_000)
     ap.add_argument("--batch", action="store_true",
                     help="64-cavity Ra sweep: batched persistent launch vs a per-cavity loop")
     return ap.parse_args()
@@ -366,6 +372,75 @@ def batch(args, pkg, torch):
                       "GBps_batched": 112 * nodes * K / t_batch / 1e9}), flush=True)
 
 
+def convergence(args, pkg, torch):
+    """Grid convergence at Ra = 1e6 (Sec. 3, Table 2): error-function meshes
+    (a = 1.5) of 257, 513 and 1025 nodes per axis, FP32, run together as one
+    batch from rest until each cavity's Nu window means (50 samples 2000 steps
+    apart) agree to 1e-6; then the observed order, the extrapolated value and
+    the GCI of every quantity, next to the values Table 2 prints."""
+    from paper_2509_01099_gb300 import analysis
+    Ns = (257, 513, 1025)
+    cavs = [dict(n=n, mesh="erf", a=1.5, Ra=1e6) for n in Ns]
+    b = pkg.Batch(cavs, precision="fp32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps, nu, re, st = b.run_to_steady_nu(tol=1e-6, sample=2000, window=50,
+                                           max_steps=args.max_steps or 12_000_000, check=False)
+    wall = time.perf_counter() - t0
+    rows = {}
+    centre = {}
+    for n, m in zip(Ns, b.members):
+        r = m.reduce()
+        f = m.fields()
+        c = n // 2
+        # T* = T + 1/2 with the cold-wall reference; u*, v* = u / u_f (Table 3 quantities)
+        centre[n] = {"T_c": float(f["T"][c, c] + 0.5), "u_c": float(f["u"][c, c] / m.info.u_f),
+                     "v_c": float(f["v"][c, c] / m.info.u_f)}
+        for k in ("Nu", "Nu_hot", "Nu_middle", "Re"):
+            rows.setdefault(k, []).append(r[k])
+    for k in ("u_c", "v_c"):
+        rows[k] = [centre[n][k] for n in Ns]
+    table = analysis.convergence_table({k: tuple(v) for k, v in rows.items()})
+    print(json.dumps({"convergence": True, "workload": "2-D cavity Ra=1e6, erf a=1.5, "
+                      "257/513/1025, FP32", "steps": steps, "status": int(st), "wall_s": wall,
+                      "window_Nu": nu, "window_Re": re, "centre": centre, "table": table}),
+          flush=True)
+    b.close()
+
+
+def series(args, pkg, torch):
+    """The 1024^2 Ra = 1e8 cavity run for 200,000 steps from rest (tanh and
+    uniform meshes, FP32 and FP16 deviation storage) with the reductions every
+    1000 steps: throughput of the whole run (CUDA events, no L2 flush: one
+    long job) and the Nu series."""
+    from synthetic import temperature_noise
+    n, total, every = 1024, args.series_steps, 1000
+    for mesh in ("tanh", "uniform"):
+        for prec in ("fp32", "fp16dev"):
+            s = make_solver(pkg, n, mesh, 1e8, prec)
+            s.set_fields(temperature_noise(s.shape, 1e-6, seed=0))
+            nus, res = [], []
+            stream = torch.cuda.current_stream()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t_dev = 0.0
+            for k in range(total // every):
+                e0.record(stream)
+                s.step(every)
+                e1.record(stream)
+                r = s.reduce(check=False)          # synchronises
+                t_dev += e0.elapsed_time(e1) / 1e3
+                nus.append(r["Nu"])
+                res.append(r["Re"])
+            mlups = n * n * total / (t_dev * 1e6)
+            print(json.dumps({"series": True, "n": n, "mesh": mesh, "precision": prec,
+                              "kernel": s.info.kernel, "steps": total, "MLUPS": mlups,
+                              "wctpdt_s": (n * n / (mlups * 1e6)) * s.info.steps_per_tf,
+                              "tf": total / s.info.steps_per_tf, "Nu_every_1000": nus,
+                              "Re_every_1000": res, "status": r["status"]}), flush=True)
+            s.close()
+
+
 def cavities_sorted(cavs):
     return sorted(cavs, key=lambda c: c["n"])
 
@@ -450,6 +525,12 @@ def main():
         return
     if args.sweep3d:
         sweep3d(args, pkg, torch, flush)
+        return
+    if args.convergence:
+        convergence(args, pkg, torch)
+        return
+    if args.series:
+        series(args, pkg, torch)
         return
     if args.batch:
         batch(args, pkg, torch)
