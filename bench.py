@@ -57,7 +57,12 @@ def parse():
     ap.add_argument("--sweep3d", action="store_true", help="time the 3-D step (256^3)")
     ap.add_argument("--convergence", action="store_true",
                     help="Ra=1e6 grid convergence on 257/513/1025 erf meshes (Table 2)")
-    ap.add_argument("--max-steps", type=int, default=0, help="step budget of --convergence")
+    ap.add_argument("--max-steps", type=int, default=0,
+                    help="step budget of --convergence / --batch-steady")
+    ap.add_argument("--validate3d", action="store_true",
+                    help="3-D cavity to steady state against the paper's 3-D table (129^3, Ra=1e5)")
+    ap.add_argument("--batch-steady", action="store_true",
+                    help="the 64-cavity sweep to a steady Nu: batch vs a costed sequential loop")
     ap.add_argument("--series", action="store_true",
                     help="1024^2 Ra=1e8 for --series-steps steps with Nu every 1000 steps")
     ap.add_argument("--series-steps", type=int, default=200_000)
@@ -441,6 +446,81 @@ def series(args, pkg, torch):
             s.close()
 
 
+def batch_steady(args, pkg, torch):
+    """The 64-cavity sweep (as --batch) run from rest to a steady Nu (window means
+    of 100 samples 1000 steps apart agreeing to 2e-4, 4M-step budget) as one
+    batch, with its wall time; the sequential per-cavity loop is costed from
+    each mesh size's measured single-cavity step time times that cavity's
+    steps to steady (running 64 cavities one after the other to steady would
+    take several times the batch's GPU time)."""
+    from synthetic import ra_sweep, temperature_noise
+    ra, ns = ra_sweep(64, seed=0)
+    cavs = [dict(n=int(n), mesh="tanh", a=1.5, Ra=float(r)) for r, n in zip(ra, ns)]
+    b = pkg.Batch(cavs, precision="fp32", autotune=True)
+    for k, m in enumerate(b.members):
+        m.set_fields(temperature_noise(m.shape, 1e-6, seed=k))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps, nu, re, st = b.run_to_steady_nu(tol=2e-4, sample=1000, window=100,
+                                           max_steps=args.max_steps or 4_000_000, check=False)
+    wall = time.perf_counter() - t0
+    b.close()
+    # single-cavity step time per mesh size (default kernel, 2000 steps, CUDA events)
+    per_step = {}
+    stream = torch.cuda.current_stream()
+    for n in sorted(set(int(x) for x in ns)):
+        s = pkg.Solver(pkg.islbm_mesh_tanh(n, 1.5), pkg.islbm_mesh_tanh(n, 1.5), Ra=1e7,
+                       precision="fp32")
+        s.set_fields(temperature_noise(s.shape, 1e-6, seed=0))
+        s.step(200)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(2000)
+        e1.record(stream)
+        e1.synchronize()
+        per_step[n] = e0.elapsed_time(e1) / 1e3 / 2000
+        s.close()
+    done = [k for k in steps if k > 0]
+    seq = sum(per_step[int(n)] * (k if k > 0 else (args.max_steps or 4_000_000))
+              for n, k in zip(ns, steps))
+    print(json.dumps({"batch_steady": True, "cavities": len(cavs), "status": int(st),
+                      "converged": len(done), "wall_s_batch": wall,
+                      "wall_s_sequential_costed": seq, "speedup": seq / wall,
+                      "steps": steps, "Ra": [float(r) for r in ra], "n": [int(n) for n in ns],
+                      "Nu": nu, "Re": re, "single_cavity_s_per_step": per_step}), flush=True)
+
+
+def validate3d(args, pkg, torch):
+    """The 3-D cavity against Table 3 of the paper's 3-D section (erf mesh, a =
+    1.5, Pr = 0.71): 129^3 at Ra = 1e5 (and 181^3 at Ra = 1e6 with --n 181), FP32,
+    from rest to the steady criterion of Sec. 3 at 1e-6 over 2000 steps."""
+    from synthetic import temperature_noise
+    cases = [(129, 1e5)] if args.n != 181 else [(181, 1e6)]
+    for n, Ra in cases:
+        xi = pkg.islbm_mesh_erf(n, 1.5)
+        s = pkg.Solver(xi, xi, xi, Ra=Ra, precision="fp32")
+        s.set_fields(temperature_noise(s.shape, 1e-6, seed=0))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = s.run_to_steady(tol=1e-6, interval=2000, max_steps=args.max_steps or 3_000_000,
+                            check=False)
+        wall = time.perf_counter() - t0
+        red = s.reduce(check=False)
+        f = s.fields()
+        c = n // 2
+        uf = s.info.u_f
+        print(json.dumps({"validate3d": True, "n": n, "Ra": Ra, "kernel": s.info.kernel,
+                          "steps": r["steps"], "status": r["status"], "wall_s": wall,
+                          "tf": r["steps"] / s.info.steps_per_tf,
+                          "Nu": red["Nu"], "Nu_hot": red["Nu_hot"], "Nu_cold": red["Nu_cold"],
+                          "Re_rms_uvw": red["Re"], "Re_rms_uv": red["Re_uv"],
+                          "Re_mean": red["Re_mean"],
+                          "T_c": float(f["T"][c, c, c] + 0.5), "u_c": float(f["u"][c, c, c] / uf),
+                          "v_c": float(f["v"][c, c, c] / uf), "w_c": float(f["w"][c, c, c] / uf)}),
+              flush=True)
+        s.close()
+
+
 def cavities_sorted(cavs):
     return sorted(cavs, key=lambda c: c["n"])
 
@@ -525,6 +605,12 @@ def main():
         return
     if args.sweep3d:
         sweep3d(args, pkg, torch, flush)
+        return
+    if args.validate3d:
+        validate3d(args, pkg, torch)
+        return
+    if args.batch_steady:
+        batch_steady(args, pkg, torch)
         return
     if args.convergence:
         convergence(args, pkg, torch)

@@ -249,6 +249,19 @@ ISLBM_API islbm_status islbm_run_to_steady(islbm_t h, double tol, long long inte
                                            long long max_steps, long long* steps_done,
                                            double* du, double* dT);
 
+/* Time averages of the fields in FP64 device accumulators (for flows that keep
+ * oscillating; not in the paper, whose runs are steady).  islbm_average_reset
+ * zeroes them (allocating (d+1) doubles per node on first use);
+ * islbm_average_add adds the current T, u, v (, w) (asynchronous);
+ * islbm_average_get writes the means to host arrays of n_x*n_y[*n_z] doubles
+ * (any may be NULL; w must be NULL in 2-D), *count (may be NULL) receives the
+ * number of states averaged; ISLBM_ERR_ARG when nothing was accumulated.
+ * Synchronises.  set_* and load leave the accumulators untouched. */
+ISLBM_API islbm_status islbm_average_reset(islbm_t h);
+ISLBM_API islbm_status islbm_average_add(islbm_t h);
+ISLBM_API islbm_status islbm_average_get(islbm_t h, double* T, double* u, double* v, double* w,
+                                         long long* count);
+
 /* Convenience views of islbm_reduce. */
 typedef struct { double vol, hot, cold, middle; } islbm_nu;
 ISLBM_API islbm_status islbm_nusselt(islbm_t h, islbm_nu* out);

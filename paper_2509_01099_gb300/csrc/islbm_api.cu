@@ -555,6 +555,7 @@ extern "C" void islbm_destroy(islbm_t s) {
   if (s->dfield) cudaFree(s->dfield);
   if (s->derr) cudaFree(s->derr);
   if (s->dsnap) cudaFree(s->dsnap);
+  if (s->davg) cudaFree(s->davg);
   if (s->hresult) cudaFreeHost(s->hresult);
   delete s;
 }
@@ -692,6 +693,7 @@ static cudaError_t build_graph(Solver* s, int parity) {
 }
 
 extern "C" islbm_status islbm_step(islbm_t s, long long n) {
+  NvtxRange range("islbm_step");
   if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_step: NULL handle");
   if (n < 0) return fail(s, ISLBM_ERR_ARG, "islbm_step: negative step count");
   // whole blocks of kGraphSteps steps are replayed from a captured graph
@@ -706,7 +708,10 @@ extern "C" islbm_status islbm_step(islbm_t s, long long n) {
     }
     CK(s, cudaEventRecord(s->ev_in, s->stream));
     CK(s, cudaStreamWaitEvent(s->side, s->ev_in, 0));
-    CK(s, cudaGraphLaunch(s->graph[s->cur], s->side));
+    {
+      NvtxRange replay("islbm_graph_replay");
+      CK(s, cudaGraphLaunch(s->graph[s->cur], s->side));
+    }
     CK(s, cudaEventRecord(s->ev_out, s->side));
     CK(s, cudaStreamWaitEvent(s->stream, s->ev_out, 0));
     n -= kGraphSteps;
@@ -745,6 +750,75 @@ extern "C" islbm_status islbm_get_fields(islbm_t s, double* rho, double* T, doub
   return ISLBM_OK;
 }
 
+// ---- time averages (FP64 accumulators on the device) ----
+
+namespace {
+__global__ void k_accumulate(double* __restrict__ acc, const double* __restrict__ src,
+                             long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    acc[i] += src[i];
+}
+__global__ void k_scale(double* __restrict__ dst, const double* __restrict__ src, double c,
+                        long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = c * src[i];
+}
+int elementwise_grid(long long n) { return (int)std::min<long long>((n + 255) / 256, 4096); }
+}  // namespace
+
+extern "C" islbm_status islbm_average_reset(islbm_t s) {
+  if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_average_reset: NULL handle");
+  const size_t bytes = (size_t)(s->dim + 1) * (size_t)s->nodes * sizeof(double);
+  if (!s->davg) {
+    cudaError_t e = cudaMalloc(&s->davg, bytes);
+    if (e != cudaSuccess) return cuda_fail(s, e, "time-average accumulators");
+  }
+  CK(s, cudaMemsetAsync(s->davg, 0, bytes, s->stream));
+  s->avg_count = 0;
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_average_add(islbm_t s) {
+  if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_average_add: NULL handle");
+  if (!s->davg) {
+    const islbm_status st = islbm_average_reset(s);
+    if (st != ISLBM_OK) return st;
+  }
+  islbm_status st = ensure_field_buffer(s);
+  if (st != ISLBM_OK) return st;
+  const size_t n = (size_t)s->nodes;
+  // dfield holds [rho][T][u][v][w]; T, u, v (, w) are contiguous from dfield + n
+  double* f = s->dfield;
+  CK(s, launch_fields(*s, nullptr, f + n, f + 2 * n, f + 3 * n, s->dim == 3 ? f + 4 * n : nullptr));
+  const long long m = (long long)(s->dim + 1) * (long long)n;
+  k_accumulate<<<elementwise_grid(m), 256, 0, s->stream>>>(s->davg, f + n, m);
+  CK(s, cudaGetLastError());
+  ++s->avg_count;
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_average_get(islbm_t s, double* T, double* u, double* v, double* w,
+                                          long long* count) {
+  if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_average_get: NULL handle");
+  if (s->dim == 2 && w) return fail(s, ISLBM_ERR_ARG, "islbm_average_get: w must be NULL in 2-D");
+  if (count) *count = s->avg_count;
+  if (s->avg_count <= 0) return fail(s, ISLBM_ERR_ARG, "islbm_average_get: nothing accumulated");
+  islbm_status st = ensure_field_buffer(s);
+  if (st != ISLBM_OK) return st;
+  const size_t n = (size_t)s->nodes;
+  const long long m = (long long)(s->dim + 1) * (long long)n;
+  k_scale<<<elementwise_grid(m), 256, 0, s->stream>>>(s->dfield, s->davg, 1.0 / (double)s->avg_count, m);
+  CK(s, cudaGetLastError());
+  double* dst[4] = {T, u, v, w};
+  for (int k = 0; k < s->dim + 1; ++k)
+    if (dst[k])
+      CK(s, cudaMemcpyAsync(dst[k], s->dfield + k * n, n * 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return ISLBM_OK;
+}
+
 extern "C" islbm_status islbm_get_populations(islbm_t s, double* f, double* g) {
   if (!s || !f || !g) return fail(s, ISLBM_ERR_ARG, "islbm_get_populations: NULL argument");
   islbm_status st = ensure_field_buffer(s);
@@ -760,6 +834,7 @@ extern "C" islbm_status islbm_get_populations(islbm_t s, double* f, double* g) {
 }
 
 extern "C" islbm_status islbm_reduce(islbm_t s, islbm_reductions* out) {
+  NvtxRange range("islbm_reduce");
   if (!s || !out) return fail(s, ISLBM_ERR_ARG, "islbm_reduce: NULL argument");
   {
     const islbm_status st = check_device_flag(s);
@@ -773,6 +848,7 @@ extern "C" islbm_status islbm_reduce(islbm_t s, islbm_reductions* out) {
 }
 
 extern "C" islbm_status islbm_steady_change(islbm_t s, double* du, double* dT) {
+  NvtxRange range("islbm_steady_change");
   if (!s || !du || !dT) return fail(s, ISLBM_ERR_ARG, "islbm_steady_change: NULL argument");
   if (!s->dsnap) {
     const size_t n = (size_t)(s->dim + 1) * (size_t)s->nodes * sizeof(double);

@@ -260,6 +260,7 @@ extern "C" int islbm_batch_tile_rows(islbm_batch_t b, int i) {
 }
 
 extern "C" islbm_status islbm_batch_step(islbm_batch_t b, long long n) {
+  NvtxRange range("islbm_batch_step");
   if (!b || n < 0) return bfail(b, ISLBM_ERR_ARG, "islbm_batch_step: handle, n >= 0");
   while (b->use_graphs && n >= kGraphSteps) {
     if (!b->graph[b->parity] && build_batch_graph(b, b->parity) != cudaSuccess) {

@@ -3,6 +3,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <vector>
@@ -10,6 +11,14 @@
 #include "../../include/islbm.h"
 
 namespace islbm {
+
+// NVTX range for profilers (nsys / ncu ranges); a no-op when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Reduction accumulator slots (FP64).  The finished vector is copied to the host.
 enum RedSlot {
@@ -99,6 +108,8 @@ struct Solver {
   double* hresult = nullptr;      // pinned host copy
   double* dfield = nullptr;       // staging for field upload / download (5 * nodes)
   double* dsnap = nullptr;        // steady-state snapshot (u, v[, w], T*), allocated on first use
+  double* davg = nullptr;         // time-average accumulators (T, u, v[, w]), FP64
+  long long avg_count = 0;        // states accumulated since the last reset
   bool snap_valid = false;
   std::string err;
   unsigned long long fingerprint = 0;

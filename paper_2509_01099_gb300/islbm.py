@@ -35,7 +35,8 @@ EXPORTS = (
     "islbm_load", "islbm_reduce_noalloc", "islbm_steady_change", "islbm_run_to_steady",
     "islbm_autotune", "islbm_batch_create", "islbm_batch_destroy", "islbm_batch_member",
     "islbm_batch_tile_rows", "islbm_batch_step", "islbm_batch_synchronize",
-    "islbm_batch_run_to_steady", "islbm_batch_run_to_steady_nu", "islbm_cnn_gemm_bf16", "islbm_cnn_im2col", "islbm_cnn_col2im",
+    "islbm_batch_run_to_steady", "islbm_batch_run_to_steady_nu", "islbm_average_reset",
+    "islbm_average_add", "islbm_average_get", "islbm_cnn_gemm_bf16", "islbm_cnn_im2col", "islbm_cnn_col2im",
     "islbm_cnn_upsample2x", "islbm_cnn_tanh", "islbm_cnn_tanh_back", "islbm_cnn_to_bf16",
     "islbm_cnn_colsum", "islbm_cnn_mse", "islbm_cnn_adam", "islbm_cnn_pack_fields",
     "islbm_cnn_unpack_fields",
@@ -138,6 +139,9 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
         "islbm_batch_tile_rows": (i, [h, i]),
         "islbm_batch_step": (i, [h, ctypes.c_longlong]),
         "islbm_batch_synchronize": (i, [h]),
+        "islbm_average_reset": (i, [h]),
+        "islbm_average_add": (i, [h]),
+        "islbm_average_get": (i, [h, dp, dp, dp, dp, P(ctypes.c_longlong)]),
         "islbm_batch_run_to_steady_nu": (i, [h, d, ctypes.c_longlong, i, ctypes.c_longlong,
                                              P(ctypes.c_longlong), dp, dp]),
         "islbm_batch_run_to_steady": (i, [h, d, ctypes.c_longlong, ctypes.c_longlong,
@@ -353,6 +357,26 @@ def islbm_run_to_steady(h, tol=1e-9, interval=2000, max_steps=10_000_000, check=
     return {"steps": steps.value, "du": du.value, "dT": dT.value, "status": st}
 
 
+def islbm_average_reset(h):
+    _check(load_library().islbm_average_reset(h), h)
+
+
+def islbm_average_add(h):
+    _check(load_library().islbm_average_add(h), h)
+
+
+def islbm_average_get(h, shape, with_w=False):
+    """Time-averaged T, u, v (, w) and the number of states averaged."""
+    nodes = int(np.prod(shape))
+    out = {k: np.empty(nodes) for k in ("T", "u", "v")}
+    if with_w:
+        out["w"] = np.empty(nodes)
+    count = ctypes.c_longlong()
+    _check(load_library().islbm_average_get(h, _dptr(out["T"]), _dptr(out["u"]), _dptr(out["v"]),
+                                            _dptr(out.get("w")), ctypes.byref(count)), h)
+    return {k: a.reshape(shape) for k, a in out.items()}, count.value
+
+
 def islbm_synchronize(h):
     _check(load_library().islbm_synchronize(h), h)
 
@@ -526,6 +550,15 @@ class Solver:
 
     def fields_device(self, rho=None, T=None, u=None, v=None, w=None):
         islbm_get_fields_device(self.h, rho, T, u, v, w)
+
+    def average_reset(self):
+        islbm_average_reset(self.h)
+
+    def average_add(self):
+        islbm_average_add(self.h)
+
+    def average(self):
+        return islbm_average_get(self.h, self.shape, with_w=self.dim == 3)
 
     def populations(self):
         return islbm_get_populations(self.h, self.info.q_flow, self.info.q_temp, self.shape)

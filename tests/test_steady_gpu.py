@@ -51,3 +51,32 @@ def test_run_to_steady_and_budget():
     b = s.reduce()
     assert abs(a["Nu"] / b["Nu"] - 1) < 1e-8
     s.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_time_average_accumulators(dim):
+    """The FP64 accumulators return the mean of the states added, and reset."""
+    xi = O.mesh_tanh(10, 1.5)
+    s = pkg.Solver(*([xi] * dim), Ra=1e6, precision="fp32")
+    s.set_fields(temperature_noise(s.shape, 1e-6, seed=1))
+    with pytest.raises(pkg.IslbmError):
+        s.average()                       # nothing accumulated yet
+    keys = ("T", "u", "v") + (("w",) if dim == 3 else ())
+    snaps = []
+    s.average_reset()
+    for _ in range(3):
+        s.step(37)
+        s.average_add()
+        f = s.fields()
+        snaps.append({k: f[k] for k in keys})
+    mean, count = s.average()
+    assert count == 3
+    for k in keys:
+        ref = (snaps[0][k] + snaps[1][k] + snaps[2][k]) / 3
+        assert np.abs(mean[k] - ref).max() <= 1e-15 * max(np.abs(ref).max(), 1e-300) * 4
+    s.average_reset()
+    s.average_add()
+    mean, count = s.average()
+    f = s.fields()
+    assert count == 1 and np.array_equal(mean["T"], f["T"])
+    s.close()
