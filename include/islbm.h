@@ -323,7 +323,10 @@ ISLBM_API islbm_status islbm_batch_synchronize(islbm_batch_t b);
 /* Step in blocks of `interval` until every cavity meets the steady criterion of
  * Sec. 3 (islbm_steady_change below tol) or max_steps have been taken;
  * steps_to_steady (host, count entries, may be NULL) receives each cavity's
- * step count at which it first met it (-1: not reached). */
+ * step count at which it first met it (-1: not reached).  A cavity that has
+ * met the criterion is taken out of the work list (its state is kept and no
+ * further steps are spent on it); all cavities are advanced again when the
+ * call returns. */
 ISLBM_API islbm_status islbm_batch_run_to_steady(islbm_batch_t b, double tol, long long interval,
                                                  long long max_steps, long long* steps_to_steady);
 
@@ -337,7 +340,9 @@ ISLBM_API islbm_status islbm_batch_run_to_steady(islbm_batch_t b, double tol, lo
  * receive the step count (-1: not reached) and the window means of that
  * window (of the last window for a cavity that did not converge).  Steps
  * continue in whole samples until every cavity is steady or the next sample
- * would pass max_steps (then ISLBM_ERR_NOT_CONVERGED).  ISLBM_ERR_ARG for
+ * would pass max_steps (then ISLBM_ERR_NOT_CONVERGED).  As in
+ * islbm_batch_run_to_steady, steady cavities leave the work list until the
+ * call returns.  ISLBM_ERR_ARG for
  * tol <= 0, sample <= 0 or window < 2.  Not in the paper, whose runs are
  * converged with the field criterion. */
 ISLBM_API islbm_status islbm_batch_run_to_steady_nu(islbm_batch_t b, double tol, long long sample,
@@ -408,6 +413,13 @@ ISLBM_API islbm_status islbm_cnn_pack_fields(const double* T, const double* u, c
 ISLBM_API islbm_status islbm_cnn_unpack_fields(const float* y, long long nodes, double T_mid,
                                                double T_scale, double u_scale, double* T,
                                                double* u, double* v, void* stream);
+
+/* Debug builds only (compiled with ISLBM_BOUNDS_CHECK): *flagged = 1 if any
+ * staged shared-memory index of the pipelined step kernels fell outside its
+ * window since the last reset (the access read element 0 instead; nothing
+ * traps).  reset != 0 clears the flags.  Release builds always report 0.
+ * The paper has no counterpart: this is a bounds checker for the kernels. */
+ISLBM_API islbm_status islbm_debug_bounds(int reset, int* flagged);
 
 /* ---- reductions without allocation ------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers of

@@ -992,3 +992,11 @@ extern "C" islbm_status islbm_load(islbm_t s, const char* path) {
   s->snap_valid = false;
   return ISLBM_OK;
 }
+
+extern "C" islbm_status islbm_debug_bounds(int reset, int* flagged) {
+  if (!flagged) return fail(nullptr, ISLBM_ERR_ARG, "islbm_debug_bounds: NULL argument");
+  const int a = bounds_flag_d2(reset), b = bounds_flag_d3(reset);
+  if (a < 0 || b < 0) return fail(nullptr, ISLBM_ERR_CUDA, "islbm_debug_bounds: reading the flags");
+  *flagged = (a | b) ? 1 : 0;
+  return ISLBM_OK;
+}

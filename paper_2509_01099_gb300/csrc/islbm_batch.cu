@@ -23,6 +23,7 @@ void set_last_error_static(const char* msg);
 
 struct islbm_batch {
   std::vector<islbm_t> members;
+  std::vector<char> active;              // members still advanced by islbm_batch_step
   std::vector<int> rows;                 // rows per thread (2 or 4) of each member's tiles
   std::vector<BatchGroup*> groups;
   cudaStream_t stream = nullptr;
@@ -94,10 +95,75 @@ cudaError_t build_batch_graph(islbm_batch* b, int parity) {
 }
 
 void sync_members(islbm_batch* b, long long steps) {
-  for (islbm_t m : b->members) {
-    m->cur = b->parity;
-    m->time += steps;
+  for (size_t i = 0; i < b->members.size(); ++i)
+    if (b->active[i]) {
+      b->members[i]->cur = b->parity;
+      b->members[i]->time += steps;
+    }
+}
+
+// (Re)build the work lists of the active members, one group per tile height;
+// the captured graphs belong to the old lists and are dropped.
+cudaError_t rebuild_groups(islbm_batch* b) {
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return e;
+  if (b->side && (e = cudaStreamSynchronize(b->side)) != cudaSuccess) return e;
+  for (int k = 0; k < 2; ++k)
+    if (b->graph[k]) {
+      cudaGraphExecDestroy(b->graph[k]);
+      b->graph[k] = nullptr;
+    }
+  for (BatchGroup* g : b->groups) delete g;
+  b->groups.clear();
+  for (int rows : {2, 4}) {
+    std::vector<Solver*> grp;
+    for (size_t i = 0; i < b->members.size(); ++i)
+      if (b->active[i] && b->rows[i] == rows) grp.push_back(b->members[i]);
+    if (grp.empty()) continue;
+    BatchGroup* g = nullptr;
+    e = make_batch_group(grp, rows, b->precision, b->members[0]->sm_count, b->stream, &g);
+    if (e != cudaSuccess) return e;
+    b->groups.push_back(g);
   }
+  return cudaSuccess;
+}
+
+// Advance every member again: a retired member's state is copied into the
+// buffer the batch reads next, so that all members share one parity.
+islbm_status reactivate_all(islbm_batch* b) {
+  bool changed = false;
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    if (b->active[i]) continue;
+    islbm_t m = b->members[i];
+    if (m->cur != b->parity) {
+      const size_t bytes = (size_t)(m->qf + m->qg) * (size_t)m->plane * m->elem;
+      const cudaError_t e = cudaMemcpyAsync(m->buf[b->parity], m->buf[m->cur], bytes,
+                                            cudaMemcpyDeviceToDevice, b->stream);
+      if (e != cudaSuccess)
+        return bfail(b, ISLBM_ERR_CUDA, std::string("batch reactivate: ") + cudaGetErrorString(e));
+      m->cur = b->parity;
+    }
+    b->active[i] = 1;
+    changed = true;
+  }
+  if (!changed) return ISLBM_OK;
+  const cudaError_t e = rebuild_groups(b);
+  return e == cudaSuccess ? ISLBM_OK
+                          : bfail(b, ISLBM_ERR_CUDA, std::string("batch regroup: ") + cudaGetErrorString(e));
+}
+
+// Stop advancing the members flagged in `retire` (a converged cavity keeps its state).
+islbm_status retire(islbm_batch* b, const std::vector<char>& retire_now) {
+  bool changed = false;
+  for (size_t i = 0; i < b->members.size(); ++i)
+    if (retire_now[i] && b->active[i]) {
+      b->active[i] = 0;
+      changed = true;
+    }
+  if (!changed) return ISLBM_OK;
+  const cudaError_t e = rebuild_groups(b);
+  return e == cudaSuccess ? ISLBM_OK
+                          : bfail(b, ISLBM_ERR_CUDA, std::string("batch regroup: ") + cudaGetErrorString(e));
 }
 
 // ---- autotuner ----
@@ -212,17 +278,10 @@ extern "C" islbm_status islbm_batch_create(int count, const islbm_cavity* cav, i
     b->members.push_back(h);
     b->rows.push_back(rows);
   }
+  b->active.assign(b->members.size(), 1);
   cudaError_t e = cudaMalloc(&b->derr, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(b->derr, 0, sizeof(int), b->stream);
-  for (int rows : {2, 4}) {
-    std::vector<Solver*> grp;
-    for (size_t i = 0; i < b->members.size(); ++i)
-      if (b->rows[i] == rows) grp.push_back(b->members[i]);
-    if (grp.empty() || e != cudaSuccess) continue;
-    BatchGroup* g = nullptr;
-    e = make_batch_group(grp, rows, precision, b->members[0]->sm_count, b->stream, &g);
-    if (e == cudaSuccess) b->groups.push_back(g);
-  }
+  if (e == cudaSuccess) e = rebuild_groups(b);
   if (e != cudaSuccess) {
     islbm_batch_destroy(b);
     return bfail(nullptr, ISLBM_ERR_CUDA, std::string("islbm_batch_create: ") + cudaGetErrorString(e));
@@ -262,6 +321,7 @@ extern "C" int islbm_batch_tile_rows(islbm_batch_t b, int i) {
 extern "C" islbm_status islbm_batch_step(islbm_batch_t b, long long n) {
   NvtxRange range("islbm_batch_step");
   if (!b || n < 0) return bfail(b, ISLBM_ERR_ARG, "islbm_batch_step: handle, n >= 0");
+  if (b->groups.empty()) return ISLBM_OK;   // every member retired
   while (b->use_graphs && n >= kGraphSteps) {
     if (!b->graph[b->parity] && build_batch_graph(b, b->parity) != cudaSuccess) {
       b->use_graphs = false;
@@ -310,9 +370,10 @@ extern "C" islbm_status islbm_batch_run_to_steady(islbm_batch_t b, double tol, l
   const size_t n = b->members.size();
   std::vector<long long> done(n, -1);
   double du, dT;
-  for (islbm_t m : b->members) {
-    const islbm_status st = islbm_steady_change(m, &du, &dT);   // snapshots
-    if (st != ISLBM_OK) return bfail(b, st, member_error(m));
+  for (size_t i = 0; i < n; ++i) {
+    if (!b->active[i]) continue;
+    const islbm_status st = islbm_steady_change(b->members[i], &du, &dT);   // snapshots
+    if (st != ISLBM_OK) return bfail(b, st, member_error(b->members[i]));
   }
   long long t = 0;
   size_t left = n;
@@ -323,6 +384,7 @@ extern "C" islbm_status islbm_batch_run_to_steady(islbm_batch_t b, double tol, l
     if (st != ISLBM_OK) return st;
     t += k;
     for (size_t i = 0; i < n; ++i) {
+      if (!b->active[i]) continue;
       st = islbm_steady_change(b->members[i], &du, &dT);
       if (st != ISLBM_OK) return bfail(b, st, member_error(b->members[i]));
       if (done[i] < 0 && k == interval && du < tol && dT < tol) {
@@ -330,9 +392,15 @@ extern "C" islbm_status islbm_batch_run_to_steady(islbm_batch_t b, double tol, l
         --left;
       }
     }
+    std::vector<char> conv(n, 0);
+    for (size_t i = 0; i < n; ++i) conv[i] = done[i] >= 0;
+    st = retire(b, conv);
+    if (st != ISLBM_OK) return st;
   }
   if (steps_to_steady)
     for (size_t i = 0; i < n; ++i) steps_to_steady[i] = done[i];
+  const islbm_status ra = reactivate_all(b);
+  if (ra != ISLBM_OK) return ra;
   return left == 0 ? ISLBM_OK
                    : bfail(b, ISLBM_ERR_NOT_CONVERGED, "islbm_batch_run_to_steady: step budget exhausted");
 }
@@ -356,6 +424,7 @@ extern "C" islbm_status islbm_batch_run_to_steady_nu(islbm_batch_t b, double tol
     if (st != ISLBM_OK) return st;
     t += sample;
     for (size_t i = 0; i < n; ++i) {
+      if (!b->active[i]) continue;
       islbm_reductions r;
       st = islbm_reduce(b->members[i], &r);
       if (st != ISLBM_OK) return bfail(b, st, member_error(b->members[i]));
@@ -377,12 +446,18 @@ extern "C" islbm_status islbm_batch_run_to_steady_nu(islbm_batch_t b, double tol
       }
       prev[i] = m;
     }
+    std::vector<char> conv(n, 0);
+    for (size_t i = 0; i < n; ++i) conv[i] = done[i] >= 0;
+    st = retire(b, conv);
+    if (st != ISLBM_OK) return st;
   }
   for (size_t i = 0; i < n; ++i) {
     if (steps_to_steady) steps_to_steady[i] = done[i];
     if (nu_mean) nu_mean[i] = nu_out[i];
     if (re_mean) re_mean[i] = re_out[i];
   }
+  const islbm_status ra = reactivate_all(b);
+  if (ra != ISLBM_OK) return ra;
   return left == 0 ? ISLBM_OK
                    : bfail(b, ISLBM_ERR_NOT_CONVERGED,
                            "islbm_batch_run_to_steady_nu: step budget exhausted");

@@ -541,6 +541,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ sm, const float4
     bm = __float_as_int(tm.w) - cx0;
   }
   auto rd = [&](int pl, int row, int cl) -> float {
+    if (!(ISLBM_IN_WINDOW(row, G::SH) && ISLBM_IN_WINDOW(cl, SW))) row = cl = 0;
     return to_f(sm[(size_t)pl * G::PLANE + row * SW + cl]);
   };
   // x-interpolated value of plane pl in staged row `row` for direction cx
@@ -1135,4 +1136,21 @@ cudaError_t make_batch_group(const std::vector<Solver*>& members, int tile_rows,
   return cudaErrorInvalidValue;
 }
 
+}  // namespace islbm
+
+namespace islbm {
+int bounds_flag_d2(int reset) {
+#ifdef ISLBM_BOUNDS_CHECK
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_bounds_flag, sizeof(int)) != cudaSuccess) return -1;
+  if (reset) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_bounds_flag, &zero, sizeof(int));
+  }
+  return v;
+#else
+  (void)reset;
+  return 0;
+#endif
+}
 }  // namespace islbm

@@ -119,6 +119,8 @@ template <typename S, typename R, bool HXa, bool HYa, bool HZa>
 __device__ __forceinline__ R own_w(const S* __restrict__ pl, const Node3<R>& n) {
   using B = Box3<S, HXa, HYa, HZa>;
   const int x = HXa ? n.lxh : n.lxn, y = HYa ? n.lyh : n.lyn, z = HZa ? n.lzh : n.lzn;
+  if (!(ISLBM_IN_WINDOW(z, B::D) && ISLBM_IN_WINDOW(y, B::H) && ISLBM_IN_WINDOW(x, B::W)))
+    return R(0);
   return (R)to_f(pl[(z * B::H + y) * B::W + x]);
 }
 
@@ -127,7 +129,11 @@ __device__ __forceinline__ R own_w(const S* __restrict__ pl, const Node3<R>& n) 
 template <typename S, typename R, int CX, int CY, int CZ, bool UNI>
 __device__ __forceinline__ R pull_w(const S* __restrict__ pl, const Node3<R>& n) {
   using B = Box3<S, CX != 0, CY != 0, CZ != 0>;
-  auto at = [&](int z, int y, int x) -> R { return (R)to_f(pl[(z * B::H + y) * B::W + x]); };
+  auto at = [&](int z, int y, int x) -> R {
+    if (!(ISLBM_IN_WINDOW(z, B::D) && ISLBM_IN_WINDOW(y, B::H) && ISLBM_IN_WINDOW(x, B::W)))
+      return R(0);
+    return (R)to_f(pl[(z * B::H + y) * B::W + x]);
+  };
   // node coordinates in this box (halo coordinates along the moving axes)
   const int lx = CX != 0 ? n.lxh : n.lxn, ly = CY != 0 ? n.lyh : n.lyn;
   const int lz = CZ != 0 ? n.lzh : n.lzn;
@@ -461,6 +467,21 @@ cudaError_t launch_step_3d_tma(Solver& s) {
     case ISLBM_BF16DEV: return launch3_tma_any<__nv_bfloat16>(s);
   }
   return cudaErrorInvalidValue;
+}
+
+int bounds_flag_d3(int reset) {
+#ifdef ISLBM_BOUNDS_CHECK
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_bounds_flag, sizeof(int)) != cudaSuccess) return -1;
+  if (reset) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_bounds_flag, &zero, sizeof(int));
+  }
+  return v;
+#else
+  (void)reset;
+  return 0;
+#endif
 }
 
 bool step_3d_tma_fits(int ny, int nz) { return ny >= kT3Y + 2 && nz >= kT3Z + 2; }

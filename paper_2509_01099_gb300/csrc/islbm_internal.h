@@ -12,6 +12,29 @@
 
 namespace islbm {
 
+// Debug builds (ISLBM_BOUNDS_CHECK, build(debug=True)) check every staged
+// shared-memory index of the pipelined kernels: an index outside its window
+// raises the translation unit's bounds flag (read by islbm_debug_bounds) and
+// reads element 0 instead; nothing traps.  Release builds compile the check
+// away.
+#ifdef __CUDACC__
+#ifdef ISLBM_BOUNDS_CHECK
+static __device__ int g_bounds_flag = 0;
+__device__ __forceinline__ bool in_window(int v, int n) {
+  if ((unsigned)v < (unsigned)n) return true;
+  atomicOr(&g_bounds_flag, 1);
+  return false;
+}
+#define ISLBM_IN_WINDOW(v, n) ::islbm::in_window((v), (n))
+#else
+#define ISLBM_IN_WINDOW(v, n) true
+#endif
+#endif
+// bounds flags of the kernel translation units (always 0 in release builds);
+// reset != 0 clears them
+int bounds_flag_d2(int reset);
+int bounds_flag_d3(int reset);
+
 // NVTX range for profilers (nsys / ncu ranges); a no-op when no tool is attached.
 struct NvtxRange {
   explicit NvtxRange(const char* name) { nvtxRangePushA(name); }

@@ -36,7 +36,7 @@ EXPORTS = (
     "islbm_autotune", "islbm_batch_create", "islbm_batch_destroy", "islbm_batch_member",
     "islbm_batch_tile_rows", "islbm_batch_step", "islbm_batch_synchronize",
     "islbm_batch_run_to_steady", "islbm_batch_run_to_steady_nu", "islbm_average_reset",
-    "islbm_average_add", "islbm_average_get", "islbm_cnn_gemm_bf16", "islbm_cnn_im2col", "islbm_cnn_col2im",
+    "islbm_average_add", "islbm_average_get", "islbm_debug_bounds", "islbm_cnn_gemm_bf16", "islbm_cnn_im2col", "islbm_cnn_col2im",
     "islbm_cnn_upsample2x", "islbm_cnn_tanh", "islbm_cnn_tanh_back", "islbm_cnn_to_bf16",
     "islbm_cnn_colsum", "islbm_cnn_mse", "islbm_cnn_adam", "islbm_cnn_pack_fields",
     "islbm_cnn_unpack_fields",
@@ -89,7 +89,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library to load: $ISLBM_LIBRARY if set (e.g. the bounds-checked
+    build), else the in-tree libislbm.so."""
+    return os.environ.get("ISLBM_LIBRARY") or _build.LIB
 
 
 def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
@@ -139,6 +141,7 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
         "islbm_batch_tile_rows": (i, [h, i]),
         "islbm_batch_step": (i, [h, ctypes.c_longlong]),
         "islbm_batch_synchronize": (i, [h]),
+        "islbm_debug_bounds": (i, [i, P(i)]),
         "islbm_average_reset": (i, [h]),
         "islbm_average_add": (i, [h]),
         "islbm_average_get": (i, [h, dp, dp, dp, dp, P(ctypes.c_longlong)]),
@@ -375,6 +378,13 @@ def islbm_average_get(h, shape, with_w=False):
     _check(load_library().islbm_average_get(h, _dptr(out["T"]), _dptr(out["u"]), _dptr(out["v"]),
                                             _dptr(out.get("w")), ctypes.byref(count)), h)
     return {k: a.reshape(shape) for k, a in out.items()}, count.value
+
+
+def islbm_debug_bounds(reset=False) -> bool:
+    """True if a bounds-checked build saw a staged index outside its window."""
+    flagged = ctypes.c_int()
+    _check(load_library().islbm_debug_bounds(1 if reset else 0, ctypes.byref(flagged)))
+    return bool(flagged.value)
 
 
 def islbm_synchronize(h):

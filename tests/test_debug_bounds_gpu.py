@@ -1,0 +1,78 @@
+"""The bounds-checked build (build(debug=True), ISLBM_BOUNDS_CHECK): every
+staged shared-memory index of the pipelined kernels is checked.  Small runs of
+the 2-D TMA kernels (FP32 and FP16 storage, 8- and 16-row tiles, one cavity and
+a batch), the 3-D pipelined kernel (FP32 and BF16 storage) and a ragged 3-D box
+must leave the flag clear and give the same fields as the release build.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from tests.helpers import gpu_available
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CASES = """
+import json, sys
+import numpy as np
+sys.path.insert(0, {root!r})
+import paper_2509_01099_gb300 as pkg
+from synthetic import temperature_noise
+out = {{}}
+pkg.islbm_debug_bounds(reset=True)
+def run(name, xis, precision, kernel, steps=40):
+    s = pkg.Solver(*xis, Ra=1e7, precision=precision, kernel=kernel)
+    s.set_fields(temperature_noise(s.shape, 1e-6, seed=3))
+    s.step(steps)
+    f = s.fields()
+    out[name] = {{"kernel": s.info.kernel, "T": float(np.abs(f["T"]).sum()),
+                 "u": float(np.abs(f["u"]).sum())}}
+    s.close()
+x2 = pkg.islbm_mesh_tanh(100, 1.5)
+run("2d_fp32_r2", (x2, x2), "fp32", "tma_r2s2")
+run("2d_fp16_r4", (x2, x2), "fp16dev", "tma_r4s2")
+run("2d_fp32_r4s3", (x2, x2), "fp32", "tma_r4s3")
+x3 = pkg.islbm_mesh_tanh(37, 1.5)
+run("3d_fp32", (x3, x3, x3), "fp32", "tma3d")
+run("3d_bf16", (x3, x3, x3), "bf16dev", "tma3d")
+b = pkg.Batch([dict(n=40, mesh="tanh", Ra=1e6), dict(n=72, mesh="tanh", Ra=1e7)], "fp32")
+b.step(40)
+b.synchronize()
+out["batch"] = {{"T": float(sum(np.abs(m.fields()["T"]).sum() for m in b.members))}}
+b.close()
+out["flagged"] = pkg.islbm_debug_bounds()
+print(json.dumps(out))
+"""
+
+
+def _run(env):
+    code = CASES.format(root=ROOT)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=900)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+@pytest.mark.skipif(not gpu_available(), reason="needs a CUDA device")
+def test_bounds_checked_build_is_clean_and_agrees():
+    from paper_2509_01099_gb300 import build as B
+    B.build()
+    debug_lib = B.build(debug=True)
+    release = _run(dict(os.environ, ISLBM_LIBRARY=B.LIB))
+    debug = _run(dict(os.environ, ISLBM_LIBRARY=debug_lib))
+    assert debug["flagged"] is False and release["flagged"] is False
+    for name, got in debug.items():
+        if name == "flagged":
+            continue
+        ref = release[name]
+        for k, v in got.items():
+            if k == "kernel":
+                assert v == ref[k]
+            else:
+                assert abs(v - ref[k]) <= 1e-6 * max(abs(ref[k]), 1e-30), (name, k, v, ref[k])
