@@ -59,6 +59,8 @@ def parse():
                     help="Ra=1e6 grid convergence on 257/513/1025 erf meshes (Table 2)")
     ap.add_argument("--max-steps", type=int, default=0,
                     help="step budget of --convergence / --batch-steady")
+    ap.add_argument("--paper-scale", action="store_true",
+                    help="the paper's timing workloads: 8193^2 and 400^3, a = 2.1, WCTpDT")
     ap.add_argument("--validate3d", action="store_true",
                     help="3-D cavity to steady state against the paper's 3-D table (129^3, Ra=1e5)")
     ap.add_argument("--batch-steady", action="store_true",
@@ -521,6 +523,32 @@ def validate3d(args, pkg, torch):
         s.close()
 
 
+def paper_scale(args, pkg, torch, flush):
+    """The paper's own timing workloads (Sec. 3 and the 3-D performance
+    paragraph): the 2-D cavity on an 8193^2 error-function mesh with a = 2.1 at
+    Ra = 1e8, and the 3-D cavity on a 400^3 mesh with a = 2.1 at Ra = 1e7, in
+    FP64 (the paper's precision), FP32 and 16-bit storage; MLUPS and WCTpDT
+    (wall-clock seconds per free-fall time), next to the paper's A100 FP64
+    WCTpDT of 1.5722e4 s and 1.456e3 s."""
+    from synthetic import temperature_noise
+    paper = {2: 1.5722e4, 3: 1.456e3}
+    for dim, n, Ra in ((2, 8193, 1e8), (3, 400, 1e7)):
+        xi = pkg.islbm_mesh_erf(n, 2.1)
+        for prec in ("fp64", "fp32", "fp16dev" if dim == 2 else "bf16dev"):
+            s = pkg.Solver(*([xi] * dim), Ra=Ra, precision=prec)
+            steps = 10 if dim == 3 or prec == "fp64" else 20
+            t = timed_steps(pkg, s, steps, 3, flush, torch)
+            nodes = n ** dim
+            mlups = nodes * steps / (t * 1e6)
+            wct = (t / steps) * s.info.steps_per_tf
+            print(json.dumps({"paper_scale": True, "dim": dim, "n": n, "a": 2.1, "Ra": Ra,
+                              "precision": prec, "kernel": s.info.kernel, "MLUPS": mlups,
+                              "wctpdt_s": wct, "steps_per_tf": s.info.steps_per_tf,
+                              "paper_wctpdt_s_a100_fp64": paper[dim],
+                              "speedup_vs_paper": paper[dim] / wct}), flush=True)
+            s.close()
+
+
 def cavities_sorted(cavs):
     return sorted(cavs, key=lambda c: c["n"])
 
@@ -605,6 +633,9 @@ def main():
         return
     if args.sweep3d:
         sweep3d(args, pkg, torch, flush)
+        return
+    if args.paper_scale:
+        paper_scale(args, pkg, torch, flush)
         return
     if args.validate3d:
         validate3d(args, pkg, torch)

@@ -5,7 +5,7 @@ its Python binding.  See include/islbm.h for the C ABI.
 """
 from .islbm import (EXPORTS, KERNEL_VARIANTS, KERNELS, LATTICES, MESH_KINDS, PRECISIONS, STENCILS,
                     Batch, IslbmError, Params, Solver, islbm_autotune, islbm_average_add,
-                    islbm_average_get, islbm_average_reset, islbm_create, islbm_default_params,
+                    islbm_average_get, islbm_average_reset, islbm_create, islbm_debug_bounds, islbm_default_params,
                     islbm_destroy, islbm_get_fields, islbm_get_fields_device,
                     islbm_get_populations, islbm_info, islbm_load, islbm_mass, islbm_mesh_erf,
                     islbm_mesh_tanh, islbm_mesh_uniform, islbm_nusselt, islbm_reduce,
