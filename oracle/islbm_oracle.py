@@ -714,13 +714,3 @@ def richardson(F_coarse, F_medium, F_fine, r=2.0):
 def gci_fine(F_medium, F_fine, p, r=2.0, Fs=1.25):
     """Grid Convergence Index of the fine mesh in percent (Sec. 3)."""
     return Fs / (r ** p - 1.0) * abs((F_fine - F_medium) / F_fine) * 100.0
-
-
-def mlups(nodes: int, steps: int, seconds: float) -> float:
-    """Million lattice updates per second (Sec. 3)."""
-    return nodes * steps / (seconds * 1e6)
-
-
-def steps_per_free_fall_time(L: float, Ma: float = 0.1) -> float:
-    """Time steps per t_f: dt/dx = Ma c_s with dx = 1/L (Sec. 3)."""
-    return L / (Ma / math.sqrt(3.0))

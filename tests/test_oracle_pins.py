@@ -416,3 +416,81 @@ def test_table3_local_orders():
         p, Finf = O.richardson(*ref[key]["values"], 2.0)
         assert abs(p - ref[key]["p"]) < 0.1, (key, p)
         assert abs(Finf / ref[key]["inf"] - 1) < 3e-3, (key, Finf)
+
+
+# ---------------------------------------------------------------------------
+# the steady criterion and the volume reductions on states with closed forms
+# ---------------------------------------------------------------------------
+
+
+def test_steady_change_closed_forms():
+    rng = np.random.default_rng(5)
+    u = [rng.standard_normal((6, 7)), rng.standard_normal((6, 7))]
+    T = rng.uniform(0.1, 0.9, (6, 7))
+    assert O.steady_change(u, u, T, T) == (0.0, 0.0)
+    # doubling every velocity changes each node by its own speed: du = 1
+    du, dT = O.steady_change([2 * c for c in u], u, T, T)
+    assert abs(du - 1.0) < 1e-15 and dT == 0.0
+    # a uniform shift c of T*: dT = c N / sum |T*|
+    du, dT = O.steady_change(u, u, T + 0.01, T)
+    assert abs(dT - 0.01 * T.size / np.abs(T).sum()) < 1e-15
+
+
+@pytest.mark.parametrize("mesh", ["uniform", "erf"])
+def test_volume_reductions_of_uniform_and_two_valued_flows(mesh):
+    """T* uniform and a uniform or half-and-half horizontal velocity: <Nu>,
+    the RMS <Re> (R10) and the mean-speed Re_mean have closed forms (the mesh is
+    symmetric, so each half of the columns carries half the volume)."""
+    n = 16
+    xi = O.mesh_uniform(n) if mesh == "uniform" else O.mesh_erf(n, 1.5)
+    p = O.Params(Ra=1e6, Pr=0.71)
+    cav = O.Cavity(xi, xi, params=p)
+    uf = cav.par.u_f
+    Tstar = 0.3                              # T* = (T - T_cold) / dT
+    T = np.full(cav.shape, p.T_cold + Tstar * (p.T_hot - p.T_cold))
+    c1, c2 = 0.02 * uf, -0.05 * uf
+    # uniform velocity
+    cav.init_fields(T, [np.full(cav.shape, c1), np.zeros(cav.shape)])
+    r = cav.reductions()
+    assert abs(r["Nu"] - (math.sqrt(p.Ra * p.Pr) * (c1 / uf) * Tstar + 1.0)) < 1e-12
+    # the buoyancy force of T* = 0.3 shifts the reported v by F / 2 rho; use T* = 0 for Re
+    T0 = np.full(cav.shape, p.T_cold)
+    cav.init_fields(T0, [np.full(cav.shape, c1), np.zeros(cav.shape)])
+    r = cav.reductions()
+    assert abs(r["Nu"] - 1.0) < 1e-14
+    assert abs(r["Re"] - math.sqrt(p.Ra / p.Pr) * abs(c1) / uf) < 1e-10
+    # two-valued: left half of the columns at c1, right half at c2
+    u = np.full(cav.shape, c1)
+    u[:, n // 2:] = c2
+    cav.init_fields(T0, [u, np.zeros(cav.shape)])
+    r = cav.reductions()
+    scale = math.sqrt(p.Ra / p.Pr) / uf
+    assert abs(r["Re"] - scale * math.sqrt((c1 ** 2 + c2 ** 2) / 2)) < 1e-10
+    assert abs(r["Re_mean"] - scale * (abs(c1) + abs(c2)) / 2) < 1e-10
+    assert r["Re"] > r["Re_mean"]          # RMS exceeds the mean for unequal speeds
+
+
+@pytest.mark.parametrize("name", ["mesh_tanh", "mesh_erf"])
+def test_stretched_meshes_shape(name):
+    """Both stretched meshes: ends at 0 and 1, exact symmetry, strictly
+    increasing, the uniform mesh j/(N+1) in the limit a -> 0, and wall
+    clustering whose end-to-centre spacing ratio is the ratio of the stretching
+    function's derivatives there: sech^2 for tanh, a Gaussian for erf."""
+    mk = getattr(O, name)
+    N, a = 401, 1.5
+    xi = mk(N, a)
+    assert xi[0] == 0.0 and xi[-1] == 1.0
+    assert np.all(xi + xi[::-1] == 1.0) and np.all(np.diff(xi) > 0)
+    lim = mk(N, 1e-5)
+    np.testing.assert_allclose(lim, np.arange(N + 2) / (N + 1), rtol=0, atol=1e-9)
+    d = np.diff(xi)
+    ratio = d[0] / d[N // 2]
+    # derivative of the stretching function at the two intervals' midpoints
+    # (midpoint differences are second-order accurate)
+    s_end, s_mid = 0.5 / (N + 1) - 0.5, (N // 2 + 0.5) / (N + 1) - 0.5
+    if name == "mesh_tanh":
+        deriv = lambda s: 1.0 / math.cosh(a * s) ** 2
+    else:
+        deriv = lambda s: math.exp(-(a * s) ** 2)
+    expect = deriv(s_end) / deriv(s_mid)
+    assert abs(ratio / expect - 1) < 1e-4, (ratio, expect)
