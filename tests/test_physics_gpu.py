@@ -65,3 +65,28 @@ def test_table3_centre_values(steady_257):
     assert abs(steady_257["u_c"] / ref["u_c"]["values"][0] - 1) < 0.15
     assert steady_257["v_c"] > 0                             # same sign, ~1e-5
     assert abs(steady_257["omega_c"] / ref["omega_c"]["values"][0] - 1) < 0.02
+
+
+def test_3d_cavity_against_the_papers_3d_table():
+    """129^3 error-function mesh (a = 1.5), Ra = 1e5, FP32, run to the Sec. 3
+    criterion (1e-6 over 2000 steps) on the pipelined 3-D kernel, against the
+    paper's 129^3 row (<Nu> 4.3406, Nu_hot = Nu_cold 4.3624, <Re> 39.4521).
+    Bounds as in 2-D plus the 3-D wall-flux offset: <Nu> and <Re> within
+    0.5%, the wall Nusselt numbers within 0.6%, hot and cold walls equal to
+    1e-4 (the steady cavity's antisymmetry)."""
+    n = 129
+    xi = pkg.islbm_mesh_erf(n, 1.5)
+    s = pkg.Solver(xi, xi, xi, Ra=1e5, precision="fp32")
+    assert s.info.kernel == pkg.KERNELS["tma3d"]
+    s.set_fields(temperature_noise(s.shape, 1e-6, seed=0))
+    r = s.run_to_steady(tol=1e-6, interval=2000, max_steps=600_000)
+    assert r["status"] == 0
+    red = s.reduce()
+    s.close()
+    assert abs(red["Nu"] / 4.3406 - 1) < 5e-3, red["Nu"]
+    assert abs(red["Nu_hot"] / 4.3624 - 1) < 6e-3, red["Nu_hot"]
+    assert abs(red["Nu_cold"] / 4.3624 - 1) < 6e-3, red["Nu_cold"]
+    assert abs(red["Nu_hot"] / red["Nu_cold"] - 1) < 1e-4
+    # <Re> with the RMS reading; both the (u, v) and the (u, v, w) forms
+    assert abs(red["Re_uv"] / 39.4521 - 1) < 5e-3, red["Re_uv"]
+    assert abs(red["Re"] / 39.4521 - 1) < 5e-3, red["Re"]
