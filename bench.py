@@ -61,6 +61,8 @@ def parse():
                     help="step budget of --convergence / --batch-steady")
     ap.add_argument("--paper-scale", action="store_true",
                     help="the paper's timing workloads: 8193^2 and 400^3, a = 2.1, WCTpDT")
+    ap.add_argument("--validate2d", action="store_true",
+                    help="2-D cavity at Ra=1e8 to steady state against Table 2's 513^2 row")
     ap.add_argument("--validate3d", action="store_true",
                     help="3-D cavity to steady state against the paper's 3-D table (129^3, Ra=1e5)")
     ap.add_argument("--batch-steady", action="store_true",
@@ -492,6 +494,37 @@ def batch_steady(args, pkg, torch):
                       "Nu": nu, "Re": re, "single_cavity_s_per_step": per_step}), flush=True)
 
 
+def validate2d(args, pkg, torch):
+    """The 2-D cavity at Ra = 1e8 against Table 2's 513^2 row (erf mesh a = 1.5,
+    Pr = 0.71; <Nu> 30.313, Nu_hot 30.3503, Nu_middle 30.3125, <Re> 542.9352),
+    FP32, from rest to a steady Nu (window means of 100 samples 1000 steps
+    apart agreeing to 1e-5)."""
+    from synthetic import temperature_noise
+    n, Ra = 513, 1e8
+    b = pkg.Batch([dict(n=n, mesh="erf", a=1.5, Ra=Ra)], precision="fp32")
+    m = b.members[0]
+    m.set_fields(temperature_noise(m.shape, 1e-6, seed=0))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps, nu, re, st = b.run_to_steady_nu(tol=1e-5, sample=1000, window=100,
+                                           max_steps=args.max_steps or 12_000_000, check=False)
+    wall = time.perf_counter() - t0
+    red = m.reduce(check=False)
+    f = m.fields()
+    c = n // 2
+    uf = m.info.u_f
+    print(json.dumps({"validate2d": True, "n": n, "Ra": Ra, "steps": steps[0], "status": int(st),
+                      "wall_s": wall, "tf": steps[0] / m.info.steps_per_tf,
+                      "window_Nu": nu[0], "window_Re": re[0], "Nu": red["Nu"],
+                      "Nu_hot": red["Nu_hot"], "Nu_cold": red["Nu_cold"],
+                      "Nu_middle": red["Nu_middle"], "Re": red["Re"],
+                      "T_c": float(f["T"][c, c] + 0.5), "u_c": float(f["u"][c, c] / uf),
+                      "v_c": float(f["v"][c, c] / uf),
+                      "paper_513": {"Nu": 30.313, "Nu_hot": 30.3503, "Nu_middle": 30.3125,
+                                    "Re": 542.9352}}), flush=True)
+    b.close()
+
+
 def validate3d(args, pkg, torch):
     """The 3-D cavity against Table 3 of the paper's 3-D section (erf mesh, a =
     1.5, Pr = 0.71): 129^3 at Ra = 1e5 (and 181^3 at Ra = 1e6 with --n 181), FP32,
@@ -636,6 +669,9 @@ def main():
         return
     if args.paper_scale:
         paper_scale(args, pkg, torch, flush)
+        return
+    if args.validate2d:
+        validate2d(args, pkg, torch)
         return
     if args.validate3d:
         validate3d(args, pkg, torch)
