@@ -90,3 +90,20 @@ def test_3d_cavity_against_the_papers_3d_table():
     # <Re> with the RMS reading; both the (u, v) and the (u, v, w) forms
     assert abs(red["Re_uv"] / 39.4521 - 1) < 5e-3, red["Re_uv"]
     assert abs(red["Re"] / 39.4521 - 1) < 5e-3, red["Re"]
+
+
+def test_2d_cavity_at_ra1e8_against_table2():
+    """513^2 error-function mesh (a = 1.5), Ra = 1e8, FP32, run to a steady Nu
+    (window means agreeing to 1e-5), against Table 2's 513^2 row.  Bounds as at
+    Ra = 1e6: the Nusselt numbers and <Re> within 0.5%."""
+    b = pkg.Batch([dict(n=513, mesh="erf", a=1.5, Ra=1e8)], precision="fp32")
+    m = b.members[0]
+    m.set_fields(temperature_noise(m.shape, 1e-6, seed=0))
+    steps, nu, re, st = b.run_to_steady_nu(tol=1e-5, sample=1000, window=100,
+                                           max_steps=9_000_000)
+    red = m.reduce()
+    b.close()
+    for key, ref in (("Nu", 30.313), ("Nu_hot", 30.3503), ("Nu_middle", 30.3125),
+                     ("Re", 542.9352)):
+        assert abs(red[key] / ref - 1) < 5e-3, (key, red[key], ref)
+    assert abs(red["Nu_hot"] / red["Nu_cold"] - 1) < 1e-4
