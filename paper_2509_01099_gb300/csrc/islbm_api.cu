@@ -6,6 +6,8 @@
 // Nu / Re reductions (Sec. 3, Sec. 4, Eq. (17), Eq. (18)).
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -174,6 +176,30 @@ std::string encode_tensor_maps(Solver* s) {
   }
   return "";
 }
+
+}  // namespace
+
+cudaError_t islbm::launch_setup_once(const void* kernel,
+                                     cudaError_t (*setup)(const void*, int*), int* value) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(kernel, dev);
+  auto it = done.find(key);
+  if (it == done.end()) {
+    int v = 1;
+    e = setup(kernel, &v);
+    if (e != cudaSuccess) return e;
+    it = done.emplace(key, v).first;
+  }
+  if (value) *value = it->second;
+  return cudaSuccess;
+}
+
+namespace {
 
 // Report (and clear) a timeout recorded by a pipelined kernel.  Synchronises.
 islbm_status check_device_flag(Solver* s) {

@@ -346,8 +346,7 @@ extern "C" islbm_status islbm_cnn_gemm_bf16(const void* A, const void* B, float*
     return ISLBM_ERR_ARG;
   const int gx = (N + GN - 1) / GN, gy = (M + GM - 1) / GM;
   // split K over blockIdx.z when the output tiles alone do not fill the GPU
-  static thread_local int sms = 0;
-  if (sms == 0) sms = device_sms();
+  const int sms = device_sms();
   const long long tiles = (long long)gx * gy;
   int split = 1;
   if (tiles < 2LL * sms && K >= 16 * GK) {

@@ -861,14 +861,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <typename S, int R, bool UNI>
 cudaError_t launch_tiled(const Solver& s, const S* in, S* out, const P2<float>& p) {
   using G = TileGeom<S, R>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_step_tiled<S, R, UNI>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::smem_bytes());
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  const cudaError_t e = launch_setup_once(
+      reinterpret_cast<const void*>(k_step_tiled<S, R, UNI>),
+      [](const void* k, int*) {
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)TileGeom<S, R>::smem_bytes());
+      },
+      nullptr);
+  if (e != cudaSuccess) return e;
   const dim3 grid((s.n[0] + kTX - 1) / kTX, (s.n[1] + G::TY - 1) / G::TY);
   k_step_tiled<S, R, UNI><<<grid, kThreads, G::smem_bytes(), s.stream>>>(in, out, p);
   return cudaGetLastError();
@@ -879,16 +879,19 @@ template <typename S, int R, int STAGES>
 cudaError_t launch_tma(const Solver& s, int cur, S* out, const P2<float>& p) {
   using G = TileGeom<S, R>;
   constexpr size_t smem = (size_t)STAGES * 14 * G::PLANE * sizeof(S) + 64;
-  static int blocks_per_sm = 0;
-  if (blocks_per_sm == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_step_tma<S, R, STAGES>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_step_tma<S, R, STAGES>,
-                                                      kThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
-  }
+  int blocks_per_sm = 0;
+  const cudaError_t e = launch_setup_once(
+      reinterpret_cast<const void*>(k_step_tma<S, R, STAGES>),
+      [](const void* k, int* bps) {
+        cudaError_t e2 = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem);
+        if (e2 == cudaSuccess)
+          e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, kThreads, smem);
+        return e2;
+      },
+      &blocks_per_sm);
+  if (e != cudaSuccess) return e;
+  if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
   const int ntiles = ((s.n[0] + kTX - 1) / kTX) * ((s.n[1] + G::TY - 1) / G::TY);
   const int grid = std::min(ntiles, s.sm_count * blocks_per_sm);
   k_step_tma<S, R, STAGES><<<grid, kThreads, smem, s.stream>>>(

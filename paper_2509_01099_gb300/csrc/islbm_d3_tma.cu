@@ -435,14 +435,14 @@ cudaError_t launch3_tma(Solver& s, int blocks) {
   const size_t table_bytes = (size_t)2 * (s.n[0] + s.n[1] + s.n[2]) * sizeof(float4);
   const int in_smem = G::smem_bytes(table_bytes) <= kMaxSmem ? 1 : 0;
   const size_t smem = G::smem_bytes(in_smem ? table_bytes : 0);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_step3_tma<S, UNI>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kMaxSmem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  const cudaError_t e = launch_setup_once(
+      reinterpret_cast<const void*>(k_step3_tma<S, UNI>),
+      [](const void* k, int*) {
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kMaxSmem);
+      },
+      nullptr);
+  if (e != cudaSuccess) return e;
   S* out = static_cast<S*>(s.buf[s.cur ^ 1]);
   const Maps3* maps = reinterpret_cast<const Maps3*>(s.tmap3[s.cur]);
   k_step3_tma<S, UNI><<<blocks, kThreads3, smem, s.stream>>>(*maps, out, make_params3<float>(s),

@@ -35,6 +35,12 @@ __device__ __forceinline__ bool in_window(int v, int n) {
 int bounds_flag_d2(int reset);
 int bounds_flag_d3(int reset);
 
+// One-time launch setup of a kernel (shared-memory attribute, occupancy query),
+// run once per (kernel, current device) under a lock; *value receives what the
+// setup stored (e.g. CTAs per SM).
+cudaError_t launch_setup_once(const void* kernel, cudaError_t (*setup)(const void*, int*),
+                              int* value);
+
 // NVTX range for profilers (nsys / ncu ranges); a no-op when no tool is attached.
 struct NvtxRange {
   explicit NvtxRange(const char* name) { nvtxRangePushA(name); }

@@ -237,3 +237,33 @@ def test_training_lowers_the_loss():
         net.backward(dy)
         net.adam(lr=3e-3)
     assert losses[-1] < 0.3 * losses[0], (losses[0], losses[-1])
+
+
+def test_pack_and_unpack_fields():
+    """Solver fields <-> network channels: pack divides by the scales in FP64
+    and rounds once to FP32; unpack is its inverse to that rounding."""
+    torch = _torch()
+    lib = _lib()
+    g = gaussian_arrays([("T", (300,)), ("u", (300,)), ("v", (300,))], seed=51)
+    T = torch.from_numpy(0.4 * g["T"]).cuda()
+    u = torch.from_numpy(0.01 * g["u"]).cuda()
+    v = torch.from_numpy(0.01 * g["v"]).cuda()
+    y = torch.empty((300, 3), device="cuda")
+    T_mid, T_scale, u_scale = 0.1, 2.0, 0.0125
+    assert lib.islbm_cnn_pack_fields(_p(T), _p(u), _p(v), 300, ctypes.c_double(T_mid),
+                                     ctypes.c_double(T_scale), ctypes.c_double(u_scale), _p(y),
+                                     _stream()) == 0
+    yy = y.cpu().numpy()
+    np.testing.assert_array_equal(yy[:, 0], ((0.4 * g["T"] - T_mid) / T_scale).astype(np.float32))
+    np.testing.assert_array_equal(yy[:, 1], (0.01 * g["u"] / u_scale).astype(np.float32))
+    T2, u2, v2 = torch.empty_like(T), torch.empty_like(u), torch.empty_like(v)
+    assert lib.islbm_cnn_unpack_fields(_p(y), 300, ctypes.c_double(T_mid),
+                                       ctypes.c_double(T_scale), ctypes.c_double(u_scale),
+                                       _p(T2), _p(u2), _p(v2), _stream()) == 0
+    for a, b in ((T2, T), (u2, u), (v2, v)):
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        assert np.abs(a - b).max() <= 2 ** -23 * np.abs(b).max() * 4
+    # a zero scale is rejected
+    assert lib.islbm_cnn_pack_fields(_p(T), _p(u), _p(v), 300, ctypes.c_double(0.0),
+                                     ctypes.c_double(0.0), ctypes.c_double(1.0), _p(y),
+                                     _stream()) != 0
