@@ -36,18 +36,14 @@ struct Store<float> {
 // stalls.  Adding uniform random bits below the kept mantissa and truncating
 // rounds up with probability equal to the discarded fraction, so the
 // expected stored value is exact.  `r` supplies 32 random bits.
-__device__ __forceinline__ float sr_to_fp16_grid(float v, unsigned r) {
-  const unsigned b = __float_as_uint(v);
-  const unsigned sign = b & 0x80000000u;
-  unsigned mag = b & 0x7fffffffu;
-  if (mag >= 0x38800000u) {            // FP16 normal range: 13 mantissa bits are dropped
-    mag = (mag + (r >> 19)) & ~0x1fffu;
-    return __uint_as_float(mag | sign);
-  }
-  // FP16 subnormal range: the grid is 2^-24
-  const float q = 5.9604644775390625e-8f;
-  const float m = __uint_as_float(mag) + (float)(r >> 8) * (q * 5.9604644775390625e-8f);
-  return __uint_as_float(__float_as_uint(m) | sign);
+__device__ __forceinline__ __half sr_to_fp16(float v, unsigned r) {
+  const float a = fabsf(v);
+  // FP16 normal range: the 13 mantissa bits dropped by the truncating conversion
+  // receive random bits first (adding to the bit pattern keeps the sign)
+  const float vn = __uint_as_float(__float_as_uint(v) + (r >> 19));
+  // FP16 subnormal range: the grid is 2^-24; add a uniform fraction of it to |v|
+  const float vs = copysignf(a + (float)(r >> 8) * 3.5527136788005009e-15f, v);
+  return __float2half_rz(a >= 6.103515625e-05f ? vn : vs);
 }
 
 template <>
@@ -56,7 +52,7 @@ struct Store<__half> {
   static __device__ __forceinline__ R ld(const __half* p) { return __half2float(__ldg(p)); }
   static __device__ __forceinline__ void st(__half* p, R v) { *p = __float2half_rn(v); }
   static __device__ __forceinline__ void st_sr(__half* p, R v, unsigned r) {
-    *p = __float2half_rz(sr_to_fp16_grid(v, r));
+    *p = sr_to_fp16(v, r);
   }
 };
 
@@ -70,11 +66,10 @@ struct Store<__nv_bfloat16> {
     *p = __float2bfloat16_rn(v);
   }
   static __device__ __forceinline__ void st_sr(__nv_bfloat16* p, R v, unsigned r) {
-    // BF16 keeps the upper 16 bits of the FP32 pattern
-    const unsigned b = __float_as_uint(v);
-    const unsigned sign = b & 0x80000000u;
-    const unsigned mag = ((b & 0x7fffffffu) + (r >> 16)) & 0xffff0000u;
-    *p = __float2bfloat16_rz(__uint_as_float(mag | sign));
+    // BF16 is the upper half of the FP32 pattern: add random bits to the lower
+    // half (the carry rounds away from zero with the dropped fraction's
+    // probability) and keep the upper half
+    *p = __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r >> 16)) >> 16));
   }
 };
 
