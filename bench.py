@@ -63,6 +63,8 @@ def parse():
                     help="the paper's timing workloads: 8193^2 and 400^3, a = 2.1, WCTpDT")
     ap.add_argument("--validate2d", action="store_true",
                     help="2-D cavity at Ra=1e8 to steady state against Table 2's 513^2 row")
+    ap.add_argument("--diagnostics", action="store_true",
+                    help="boundary layers, their Ra scaling and the divergence of steady cavities")
     ap.add_argument("--validate3d", action="store_true",
                     help="3-D cavity to steady state against the paper's 3-D table (129^3, Ra=1e5)")
     ap.add_argument("--batch-steady", action="store_true",
@@ -525,6 +527,44 @@ def validate2d(args, pkg, torch):
     b.close()
 
 
+def diagnostics(args, pkg, torch):
+    """Post-processing of steady 2-D cavities (Sec. 3): erf meshes (a = 1.5) of
+    257^2 at Ra = 1e6 and 513^2 at Ra = 1e7 and 1e8, FP32, run as one batch to a
+    steady Nu (window means agreeing to 1e-5); boundary-layer thicknesses at
+    the hot wall from the mid-height band 0.4 <= y* <= 0.6 by the 99% and slope
+    methods, their Ra exponents (the paper: -0.25 for both at Pr = 0.71), and
+    the statistics of the velocity divergence |div* u*|."""
+    import numpy as np
+    from paper_2509_01099_gb300 import analysis as A
+    from synthetic import temperature_noise
+    cases = [(257, 1e6), (513, 1e7), (513, 1e8)]
+    b = pkg.Batch([dict(n=n, mesh="erf", a=1.5, Ra=ra) for n, ra in cases], precision="fp32")
+    for k, m in enumerate(b.members):
+        m.set_fields(temperature_noise(m.shape, 1e-6, seed=k))
+    steps, nu, re, st = b.run_to_steady_nu(tol=1e-5, sample=1000, window=100,
+                                           max_steps=args.max_steps or 9_000_000, check=False)
+    rows = []
+    for (n, ra), m, k in zip(cases, b.members, steps):
+        f = m.fields()
+        x = A.node_positions(pkg.islbm_mesh_erf(n, 1.5))
+        uf = m.info.u_f
+        Ts, us, vs = f["T"] + 0.5, f["u"] / uf, f["v"] / uf
+        Tb = A.band_profiles(Ts, x)
+        vb = A.band_profiles(vs, x)
+        bl = A.boundary_layers(x, Tb, vb)
+        div = np.abs(A.divergence_2d(us, vs, x, x))
+        rows.append({"n": n, "Ra": ra, "steps": k, **bl,
+                     "div_median": float(np.median(div)), "div_p99": float(np.percentile(div, 99)),
+                     "div_frac_below_1e-4": float((div < 1e-4).mean())})
+    ras = [r["Ra"] for r in rows]
+    fits = {key: A.power_law(ras, [r[key] for r in rows])[0]
+            for key in ("delta_T_99", "delta_V_99", "delta_T_slope", "delta_V_slope")}
+    print(json.dumps({"diagnostics": True, "status": int(st), "rows": rows,
+                      "exponents": fits, "paper_exponents": {"delta_T": -0.25, "delta_V": -0.25}}),
+          flush=True)
+    b.close()
+
+
 def validate3d(args, pkg, torch):
     """The 3-D cavity against Table 3 of the paper's 3-D section (erf mesh, a =
     1.5, Pr = 0.71): 129^3 at Ra = 1e5 (and 181^3 at Ra = 1e6 with --n 181), FP32,
@@ -672,6 +712,9 @@ def main():
         return
     if args.validate2d:
         validate2d(args, pkg, torch)
+        return
+    if args.diagnostics:
+        diagnostics(args, pkg, torch)
         return
     if args.validate3d:
         validate3d(args, pkg, torch)

@@ -37,3 +37,76 @@ def convergence_table(values, ratio: float = 2.0) -> dict:
         except (ValueError, ZeroDivisionError):
             out[name] = {"values": [c, m, f], "p": None, "inf": None, "gci_percent": None}
     return out
+
+
+# ---------------------------------------------------------------------------
+# Post-processing diagnostics of steady 2-D fields (Sec. 3): mid-height band
+# profiles, boundary-layer thicknesses by the 99% and slope methods, their
+# Rayleigh-number scaling, and the velocity divergence.  Coordinates are the
+# nondimensional node positions x* in (0, 1); fields are [ny][nx] arrays.
+# ---------------------------------------------------------------------------
+
+import numpy as np  # noqa: E402
+
+
+def node_positions(xi) -> np.ndarray:
+    """x* of the fluid nodes of a ghost-node mesh (walls half a lattice unit outside)."""
+    xi = np.asarray(xi, dtype=np.float64)
+    X = (xi - xi[0]) / (xi[1] - xi[0])            # lattice units, ghost at 0
+    L = X[-2] - X[1] + 1.0
+    return (X[1:-1] - X[1] + 0.5) / L
+
+
+def band_profiles(field, y_star, band=(0.4, 0.6), weights=None):
+    """Average of a [ny][nx] field over the rows with band[0] <= y* <= band[1]."""
+    rows = (y_star >= band[0]) & (y_star <= band[1])
+    w = np.ones(rows.sum()) if weights is None else np.asarray(weights)[rows]
+    return (np.asarray(field)[rows] * w[:, None]).sum(axis=0) / w.sum()
+
+
+def _first_crossing(x, f, level):
+    """x where f first reaches `level` moving away from x[0] (linear interpolation)."""
+    for k in range(1, len(f)):
+        if (f[k - 1] - level) * (f[k] - level) <= 0 and f[k] != f[k - 1]:
+            return x[k - 1] + (level - f[k - 1]) * (x[k] - x[k - 1]) / (f[k] - f[k - 1])
+    return float("nan")
+
+
+def boundary_layers(x, T, v, T_wall=1.0):
+    """Thermal and velocity boundary-layer thicknesses at the hot wall x* = 0 from
+    band-averaged profiles T*(x*), v*(x*):
+      99% method: delta_T where T* has covered 99% of the wall-to-core difference
+      (core: the value at x* = 1/2); delta_V where v* first reaches 99% of its maximum.
+      slope method: delta_T = (T_wall - T_core) / |dT*/dx*| at the wall;
+      delta_V = v_max / |dv*/dx*| at the wall (no slip: v = 0 at x* = 0)."""
+    x, T, v = (np.asarray(a, dtype=np.float64) for a in (x, T, v))
+    half = np.argmin(np.abs(x - 0.5))
+    T_core = T[half]
+    near = x < 0.5
+    xs, Ts, vs = np.concatenate(([0.0], x[near])), np.concatenate(([T_wall], T[near])), \
+        np.concatenate(([0.0], v[near]))
+    dT99 = _first_crossing(xs, Ts, T_wall - 0.99 * (T_wall - T_core))
+    imax = int(np.argmax(vs))
+    dV99 = _first_crossing(xs[:imax + 1], vs[:imax + 1], 0.99 * vs[imax])
+    # one-sided wall gradients from the wall value and the first two nodes (quadratic)
+    h1, h2 = xs[1], xs[2]
+    def wall_slope(f0, f1, f2):
+        return (f1 - f0) * h2 / (h1 * (h2 - h1)) - (f2 - f0) * h1 / (h2 * (h2 - h1))
+    gT = wall_slope(Ts[0], Ts[1], Ts[2])
+    gV = wall_slope(vs[0], vs[1], vs[2])
+    return {"delta_T_99": dT99, "delta_V_99": dV99,
+            "delta_T_slope": abs(T_wall - T_core) / abs(gT), "delta_V_slope": vs[imax] / abs(gV),
+            "T_core": T_core, "v_max": vs[imax]}
+
+
+def power_law(ra, delta):
+    """Exponent p and prefactor c of delta = c Ra^p (least squares in log-log)."""
+    p, lc = np.polyfit(np.log(np.asarray(ra, float)), np.log(np.asarray(delta, float)), 1)
+    return float(p), float(np.exp(lc))
+
+
+def divergence_2d(u, v, x, y):
+    """du/dx + dv/dy on the non-uniform node positions (second-order centred
+    differences in the interior, one-sided at the first and last nodes)."""
+    return np.gradient(np.asarray(u, float), np.asarray(x, float), axis=1) + \
+        np.gradient(np.asarray(v, float), np.asarray(y, float), axis=0)

@@ -39,3 +39,38 @@ def test_exact_power_law_is_recovered():
 def test_degenerate_rows_report_none():
     t = A.convergence_table({"flat": (1.0, 1.0, 1.0)})["flat"]
     assert t["p"] is None and t["inf"] is None
+
+
+def test_boundary_layer_methods_on_closed_forms():
+    # T* = 1 - (1 - Tc) (1 - exp(-x/d)) and v* = V (x/d) exp(1 - x/d): the slope
+    # method recovers d for T (wall slope (1 - Tc)/d) and d for v (v_max = V at
+    # x = d, wall slope V e / d -> delta_V = d / e); the 99% points are
+    # d ln(100) for T and the first crossing below the maximum for v.
+    import numpy as np
+    d, Tc, V = 0.02, 0.5, 0.3
+    x = np.linspace(0.0005, 0.5, 4000)
+    T = 1 - (1 - Tc) * (1 - np.exp(-x / d))
+    v = V * (x / d) * np.exp(1 - x / d)
+    bl = A.boundary_layers(x, T, v)
+    assert abs(bl["delta_T_slope"] - d) < 1e-3 * d
+    assert abs(bl["delta_V_slope"] - d / math.e) < 1e-3 * d
+    assert abs(bl["delta_T_99"] - d * math.log(100)) < 1e-3 * d
+    # 99% of the maximum of s e^(1-s) on the rising side: s = 0.86484...
+    assert abs(bl["delta_V_99"] - 0.864843 * d) < 2e-3 * d
+
+
+def test_power_law_and_divergence():
+    import numpy as np
+    ra = np.array([1e6, 1e7, 1e8])
+    p, c = A.power_law(ra, 3.0 * ra ** -0.25)
+    assert abs(p + 0.25) < 1e-12 and abs(c - 3.0) < 1e-9
+    x = np.sort(np.random.default_rng(1).uniform(0, 1, 40))
+    y = np.sort(np.random.default_rng(2).uniform(0, 1, 30))
+    X, Y = np.meshgrid(x, y)
+    # a divergence-free field (u, v) = (x, -y) and one with divergence 2: (x, y)
+    assert np.abs(A.divergence_2d(X, -Y, x, y)).max() < 1e-12
+    assert np.abs(A.divergence_2d(X, Y, x, y) - 2).max() < 1e-12
+    # node positions of the uniform mesh: cell centres
+    from oracle import islbm_oracle as O
+    np.testing.assert_allclose(A.node_positions(O.mesh_uniform(8)), (np.arange(8) + 0.5) / 8,
+                               rtol=0, atol=1e-15)
