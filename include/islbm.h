@@ -421,6 +421,15 @@ ISLBM_API islbm_status islbm_cnn_unpack_fields(const float* y, long long nodes, 
  * The paper has no counterpart: this is a bounds checker for the kernels. */
 ISLBM_API islbm_status islbm_debug_bounds(int reset, int* flagged);
 
+/* Self-test of the bounded device waits of the pipelined step kernels (the
+ * paper has no counterpart): one CTA waits on an mbarrier that nothing
+ * arrives at, gives up after the same poll limit as the step kernels (2^22
+ * polls, well under a second), raises a device flag and returns.  Returns
+ * ISLBM_ERR_TIMEOUT when the flag was raised (the expected outcome),
+ * ISLBM_OK if the wait somehow completed, ISLBM_ERR_CUDA / ISLBM_ERR_OOM on a
+ * CUDA failure.  Synchronises `stream`; the context stays usable. */
+ISLBM_API islbm_status islbm_selftest_wait_timeout(void* stream);
+
 /* ---- reductions without allocation ------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers of
  * this library that cannot allocate device memory: code that runs while its

@@ -36,7 +36,8 @@ EXPORTS = (
     "islbm_autotune", "islbm_batch_create", "islbm_batch_destroy", "islbm_batch_member",
     "islbm_batch_tile_rows", "islbm_batch_step", "islbm_batch_synchronize",
     "islbm_batch_run_to_steady", "islbm_batch_run_to_steady_nu", "islbm_average_reset",
-    "islbm_average_add", "islbm_average_get", "islbm_debug_bounds", "islbm_cnn_gemm_bf16", "islbm_cnn_im2col", "islbm_cnn_col2im",
+    "islbm_average_add", "islbm_average_get", "islbm_debug_bounds", "islbm_selftest_wait_timeout",
+    "islbm_cnn_gemm_bf16", "islbm_cnn_im2col", "islbm_cnn_col2im",
     "islbm_cnn_upsample2x", "islbm_cnn_tanh", "islbm_cnn_tanh_back", "islbm_cnn_to_bf16",
     "islbm_cnn_colsum", "islbm_cnn_mse", "islbm_cnn_adam", "islbm_cnn_pack_fields",
     "islbm_cnn_unpack_fields",
@@ -142,6 +143,7 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
         "islbm_batch_step": (i, [h, ctypes.c_longlong]),
         "islbm_batch_synchronize": (i, [h]),
         "islbm_debug_bounds": (i, [i, P(i)]),
+        "islbm_selftest_wait_timeout": (i, [vp]),
         "islbm_average_reset": (i, [h]),
         "islbm_average_add": (i, [h]),
         "islbm_average_get": (i, [h, dp, dp, dp, dp, P(ctypes.c_longlong)]),
@@ -385,6 +387,13 @@ def islbm_debug_bounds(reset=False) -> bool:
     flagged = ctypes.c_int()
     _check(load_library().islbm_debug_bounds(1 if reset else 0, ctypes.byref(flagged)))
     return bool(flagged.value)
+
+
+def islbm_selftest_wait_timeout(stream=None) -> int:
+    """Status of the bounded-wait self-test (ISLBM_ERR_TIMEOUT = 6 is the expected outcome)."""
+    if stream is None:
+        stream = _current_stream()
+    return load_library().islbm_selftest_wait_timeout(stream)
 
 
 def islbm_synchronize(h):

@@ -1,0 +1,31 @@
+"""Failure detection on the GPU without a fault: the bounded waits of the
+pipelined kernels give up on a barrier that never completes, report
+ISLBM_ERR_TIMEOUT through the device flag, and leave the context usable."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import islbm_oracle as O
+from synthetic import temperature_noise
+from tests.helpers import gpu_available
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not gpu_available(), reason="needs a CUDA device")]
+
+
+def test_bounded_wait_times_out_and_the_context_survives():
+    import paper_2509_01099_gb300 as pkg
+    t0 = time.perf_counter()
+    st = pkg.islbm_selftest_wait_timeout()
+    elapsed = time.perf_counter() - t0
+    assert st == 6, st                       # ISLBM_ERR_TIMEOUT
+    assert elapsed < 10.0, elapsed           # the poll limit is well under a second
+    # the same process keeps computing correctly afterwards
+    xi = O.mesh_tanh(24, 1.5)
+    s = pkg.Solver(xi, xi, Ra=1e5, precision="fp32")
+    s.set_fields(temperature_noise(s.shape, 1e-6, seed=0))
+    s.step(100)
+    r = s.reduce()
+    s.close()
+    assert r["status"] == 0 and np.isfinite(r["Nu"])
