@@ -423,8 +423,8 @@ ISLBM_API islbm_status islbm_debug_bounds(int reset, int* flagged);
 
 /* Self-test of the bounded device waits of the pipelined step kernels (the
  * paper has no counterpart): one CTA waits on an mbarrier that nothing
- * arrives at, gives up after the same poll limit as the step kernels (2^22
- * polls, well under a second), raises a device flag and returns.  Returns
+ * arrives at, gives up after the same limit as the step kernels (one second
+ * of the GPU's global timer), raises a device flag and returns.  Returns
  * ISLBM_ERR_TIMEOUT when the flag was raised (the expected outcome),
  * ISLBM_OK if the wait somehow completed, ISLBM_ERR_CUDA / ISLBM_ERR_OOM on a
  * CUDA failure.  Synchronises `stream`; the context stays usable. */

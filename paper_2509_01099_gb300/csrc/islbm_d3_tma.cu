@@ -95,12 +95,15 @@ __device__ __forceinline__ int pair_first(int j) {
   return j == 0 ? 0 : (j <= 9 ? 2 * j - 1 : (j == 10 ? 19 : 2 * j - 2));
 }
 
-// Bounded wait that also gives up as soon as another thread raised the abort flag.
+// Bounded wait (the limits of mbar_wait) that also gives up as soon as another
+// thread raised the abort flag.
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, unsigned phase,
                                               const volatile int* abort) {
-  for (int i = 0; i < (1 << 22); ++i) {
+  if (mbar_try_wait(bar, phase)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < kWaitMaxPolls; ++i) {
     if (mbar_try_wait(bar, phase)) return true;
-    if ((i & 63) == 63 && *abort) return false;
+    if ((i & 63) == 63 && (*abort || global_ns() - t0 > kWaitLimitNs)) return false;
   }
   return false;
 }

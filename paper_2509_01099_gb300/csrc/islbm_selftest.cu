@@ -1,6 +1,7 @@
 // Self-test of the bounded waits used by the pipelined step kernels: a CTA
-// waits on an mbarrier that nothing arrives at, gives up after the poll
-// limit, raises the device error flag and returns.  The host sees
+// waits on an mbarrier that nothing arrives at, gives up after the wait
+// limit (one second of the global timer), raises the device error flag and
+// returns.  The host sees
 // ISLBM_ERR_TIMEOUT and the context stays usable.  The paper has no
 // counterpart.
 #include "islbm_internal.h"

@@ -44,10 +44,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
   return ok != 0;
 }
 
-// Bounded wait: gives up after 2^22 polls (well under a second).
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// Limits of every bounded wait: one second of the global timer, with a poll
+// count as a backstop should the timer not advance.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+constexpr int kWaitMaxPolls = 1 << 24;
+
+// Bounded wait: true when the phase completed, false after the limits above.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned phase) {
-  for (int i = 0; i < (1 << 22); ++i)
+  if (mbar_try_wait(bar, phase)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < kWaitMaxPolls; ++i) {
     if (mbar_try_wait(bar, phase)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
   return false;
 }
 

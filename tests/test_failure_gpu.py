@@ -20,7 +20,7 @@ def test_bounded_wait_times_out_and_the_context_survives():
     st = pkg.islbm_selftest_wait_timeout()
     elapsed = time.perf_counter() - t0
     assert st == 6, st                       # ISLBM_ERR_TIMEOUT
-    assert elapsed < 10.0, elapsed           # the poll limit is well under a second
+    assert elapsed < 5.0, elapsed            # the wait limit is one second
     # the same process keeps computing correctly afterwards
     xi = O.mesh_tanh(24, 1.5)
     s = pkg.Solver(xi, xi, Ra=1e5, precision="fp32")
