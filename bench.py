@@ -85,8 +85,9 @@ def peaks():
 
 
 KERNEL_SOURCES = {
-    2: ("islbm_d2.cu", "islbm_store.cuh", "islbm_tma.cuh"),
-    3: ("islbm_d3_tma.cu", "islbm_d3_common.cuh", "islbm_store.cuh", "islbm_tma.cuh"),
+    2: ("islbm_d2.cu", "islbm_lanes.cuh", "islbm_store.cuh", "islbm_tma.cuh"),
+    3: ("islbm_d3_tma.cu", "islbm_d3_common.cuh", "islbm_lanes.cuh", "islbm_store.cuh",
+        "islbm_tma.cuh"),
 }
 
 

@@ -484,9 +484,9 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
   if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: reduction result");
   e = cudaMallocHost(&s->hresult, RED_STRIDE * sizeof(double));
   if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: pinned result");
-  e = cudaMalloc(&s->derr, sizeof(int));
+  e = cudaMalloc(&s->derr, kDerrInts * sizeof(int));
   if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: error flag");
-  e = cudaMemsetAsync(s->derr, 0, sizeof(int), s->stream);
+  e = cudaMemsetAsync(s->derr, 0, kDerrInts * sizeof(int), s->stream);
   if (e != cudaSuccess) return cleanup(ISLBM_ERR_CUDA, "islbm_create: error flag");
   if (s->variant >= KV_TMA_R4S2) {
     const std::string m = encode_tensor_maps(s);

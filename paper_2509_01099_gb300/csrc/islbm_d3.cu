@@ -59,13 +59,14 @@ __device__ __forceinline__ R pull3(const S* __restrict__ pl, int x, int y, int z
   }
   const S* o = pl + origin + (size_t)base0 * st0;
   const R a0 = __ldg(w0), a1 = __ldg(w0 + 1), a2 = __ldg(w0 + 2);
-  if (na == 1) return a0 * St::ld(o) + a1 * St::ld(o + st0) + a2 * St::ld(o + 2 * st0);
+  if (na == 1) return lin3(a0, a1, a2, St::ld(o), St::ld(o + st0), St::ld(o + 2 * st0));
   o += (size_t)base1 * st1;
   R acc = R(0);
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     const S* r = o + l * st1;
-    acc += __ldg(w1 + l) * (a0 * St::ld(r) + a1 * St::ld(r + st0) + a2 * St::ld(r + 2 * st0));
+    acc = lfma(__ldg(w1 + l), lin3(a0, a1, a2, St::ld(r), St::ld(r + st0), St::ld(r + 2 * st0)),
+               acc);
   }
   return acc;
 }

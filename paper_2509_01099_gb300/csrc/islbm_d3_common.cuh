@@ -3,6 +3,7 @@
 #pragma once
 
 #include "islbm_internal.h"
+#include "islbm_lanes.cuh"
 #include "islbm_store.cuh"
 
 namespace islbm {
@@ -54,7 +55,7 @@ __device__ __forceinline__ void collide3(R (&f)[19], R (&g)[7], const P3<R>& p, 
   const R Tr = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
   const R T = Tr;   // T - T_s
   const R Fy = rho * p.gbeta * (Tr + p.Fb);
-  const R inv = R(1) / rho;
+  const R inv = lrcp(rho);
   const R ux = jx * inv, uy = (jy + R(0.5) * Fy) * inv, uz = jz * inv;
   const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
   const R rusq = rho * (ux2 + uy2 + uz2);

@@ -145,17 +145,17 @@ __device__ __forceinline__ R pull_w(const S* __restrict__ pl, const Node3<R>& n)
   if (CX != 0 && CY == 0 && CZ == 0) {
     const float4 t = n.tx[kx];
     const int b = n.bx[kx];
-    return t.x * at(lz, ly, b) + t.y * at(lz, ly, b + 1) + t.z * at(lz, ly, b + 2);
+    return dot3(t, at(lz, ly, b), at(lz, ly, b + 1), at(lz, ly, b + 2));
   }
   if (CX == 0 && CY != 0 && CZ == 0) {
     const float4 t = n.ty[ky];
     const int b = n.by[ky];
-    return t.x * at(lz, b, lx) + t.y * at(lz, b + 1, lx) + t.z * at(lz, b + 2, lx);
+    return dot3(t, at(lz, b, lx), at(lz, b + 1, lx), at(lz, b + 2, lx));
   }
   if (CX == 0 && CY == 0 && CZ != 0) {
     const float4 t = n.tz[kz];
     const int b = n.bz[kz];
-    return t.x * at(b, ly, lx) + t.y * at(b + 1, ly, lx) + t.z * at(b + 2, ly, lx);
+    return dot3(t, at(b, ly, lx), at(b + 1, ly, lx), at(b + 2, ly, lx));
   }
   R acc = R(0);
   if (CZ == 0) {   // x inside, y outside
@@ -164,24 +164,24 @@ __device__ __forceinline__ R pull_w(const S* __restrict__ pl, const Node3<R>& n)
     const R wl[3] = {w.x, w.y, w.z};
 #pragma unroll
     for (int l = 0; l < 3; ++l)
-      acc += wl[l] * (a.x * at(lz, b1 + l, b0) + a.y * at(lz, b1 + l, b0 + 1) +
-                      a.z * at(lz, b1 + l, b0 + 2));
+      acc = lfma(wl[l], dot3(a, at(lz, b1 + l, b0), at(lz, b1 + l, b0 + 1), at(lz, b1 + l, b0 + 2)),
+                 acc);
   } else if (CY == 0) {   // x inside, z outside
     const float4 a = n.tx[kx], w = n.tz[kz];
     const int b0 = n.bx[kx], b1 = n.bz[kz];
     const R wl[3] = {w.x, w.y, w.z};
 #pragma unroll
     for (int l = 0; l < 3; ++l)
-      acc += wl[l] * (a.x * at(b1 + l, ly, b0) + a.y * at(b1 + l, ly, b0 + 1) +
-                      a.z * at(b1 + l, ly, b0 + 2));
+      acc = lfma(wl[l], dot3(a, at(b1 + l, ly, b0), at(b1 + l, ly, b0 + 1), at(b1 + l, ly, b0 + 2)),
+                 acc);
   } else {   // y inside, z outside
     const float4 a = n.ty[ky], w = n.tz[kz];
     const int b0 = n.by[ky], b1 = n.bz[kz];
     const R wl[3] = {w.x, w.y, w.z};
 #pragma unroll
     for (int l = 0; l < 3; ++l)
-      acc += wl[l] * (a.x * at(b1 + l, b0, lx) + a.y * at(b1 + l, b0 + 1, lx) +
-                      a.z * at(b1 + l, b0 + 2, lx));
+      acc = lfma(wl[l], dot3(a, at(b1 + l, b0, lx), at(b1 + l, b0 + 1, lx), at(b1 + l, b0 + 2, lx)),
+                 acc);
   }
   return acc;
 }

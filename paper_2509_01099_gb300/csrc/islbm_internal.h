@@ -113,6 +113,8 @@ struct Physics {
   double mid_inv_dx;  // 1/(X_{m+1}-X_m) (even n) or 1/(X_{m+1}-X_{m-1}) (odd n)
 };
 
+constexpr int kDerrInts = 4;
+
 struct Solver {
   int dim = 2, lattice = 0, precision = 1, stencil = 0;
   int n[3] = {1, 1, 1};
@@ -144,7 +146,9 @@ struct Solver {
   unsigned long long fingerprint = 0;
   int variant = KV_DIRECT;        // step kernel of the 2-D FP32/16-bit path
   int sm_count = 0;
-  int* derr = nullptr;            // device error flag of the pipelined kernels
+  // device words of the pipelined kernels: [0] error flag, [1] tiles claimed,
+  // [2] CTAs finished (the 2-D TMA kernel's dynamic schedule; zero between launches)
+  int* derr = nullptr;
   alignas(128) unsigned char tmap[2][128];   // TMA descriptors of buf[0] / buf[1]
   alignas(128) unsigned char tmap3[2][7][128];   // 3-D: one descriptor per box shape
   // CUDA graphs of kGraphSteps steps, one per starting buffer, replayed on a
