@@ -244,15 +244,15 @@ __global__ void __launch_bounds__(kThreads3, kMinBlocks3)
   if (warp == kConsumerWarps3) {
     // ---------------- producer ----------------
     if (lane == 0) {
-      long long j = 0;
+      unsigned j = 0;   // pair jobs issued (32-bit: cheap slot and phase arithmetic)
       bool stop = false;
       for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         int x0, y0, z0, sy0, sz0;
         origin(t, x0, y0, z0, sy0, sz0);
         for (int q = 0; q < kPairs3; ++q, ++j) {
-          const int s = (int)(j % kStages3);
-          if (j >= kStages3 &&
-              !wait_or_abort(&empty[s], (unsigned)((j / kStages3) - 1) & 1u, abort)) {
+          const int s = (int)(j % (unsigned)kStages3);
+          if (j >= (unsigned)kStages3 &&
+              !wait_or_abort(&empty[s], ((j / (unsigned)kStages3) - 1u) & 1u, abort)) {
             if (!*abort) atomicExch(err, 1);
             *abort = 1;
             stop = true;
@@ -269,9 +269,9 @@ __global__ void __launch_bounds__(kThreads3, kMinBlocks3)
         }
       }
       // wait (bounded) for the last copy issued into every slot
-      for (int s = 0; s < kStages3 && s < j; ++s) {
-        const long long last = j - 1 - ((j - 1 - s) % kStages3);
-        mbar_wait(&full[s], (unsigned)(last / kStages3) & 1u);
+      for (int s = 0; s < kStages3 && (unsigned)s < j; ++s) {
+        const unsigned last = j - 1u - ((j - 1u - (unsigned)s) % (unsigned)kStages3);
+        mbar_wait(&full[s], (last / (unsigned)kStages3) & 1u);
       }
     }
   } else {
@@ -279,7 +279,8 @@ __global__ void __launch_bounds__(kThreads3, kMinBlocks3)
     const int c = threadIdx.x % kT3X, ry = (threadIdx.x / kT3X) % kT3Y;
     const int rz = threadIdx.x / (kT3X * kT3Y);
     const long long P = p.plane;
-    long long j = 0;
+    // ring slot and completed ring cycles at the first pair of the current tile
+    unsigned s0 = 0, c0 = 0;
     bool stop = false;
     for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
       int x0, y0, z0, sy0, sz0;
@@ -314,6 +315,9 @@ __global__ void __launch_bounds__(kThreads3, kMinBlocks3)
       const bool wxm = xc == 0, wxp = xc == p.nx - 1, wym = yc == 0, wyp = yc == p.ny - 1;
       const bool wzm = zc == 0, wzp = zc == p.nz - 1;
       R f[19], g[7];
+      // ring slot and phase of pair q of this tile
+      auto slot_of = [&](int q) { return (s0 + (unsigned)q) % (unsigned)kStages3; };
+      auto phase_of = [&](int q) { return (c0 + (s0 + (unsigned)q) / (unsigned)kStages3) & 1u; };
 #pragma unroll
       for (int qg = 0; qg < kPairs3; qg += kGroup3) {
         // wait for every pair of the group, then pull them together (their
@@ -322,8 +326,7 @@ __global__ void __launch_bounds__(kThreads3, kMinBlocks3)
         bool ok = true;
 #pragma unroll
         for (int u = 0; u < kGroup3; ++u) {
-          const long long jj = j + qg + u;
-          ok = ok && wait_or_abort(&full[jj % kStages3], (unsigned)(jj / kStages3) & 1u, abort);
+          ok = ok && wait_or_abort(&full[slot_of(qg + u)], phase_of(qg + u), abort);
         }
         if (!ok) {
           if (!*abort) atomicExch(err, 1);
@@ -334,7 +337,7 @@ __global__ void __launch_bounds__(kThreads3, kMinBlocks3)
 #pragma unroll
         for (int u = 0; u < kGroup3; ++u) {
         const int q = qg + u;
-        const int s = (int)((j + q) % kStages3);
+        const int s = (int)slot_of(q);
         const S* a = reinterpret_cast<const S*>(smem_raw + (size_t)s * G::SLOT);
 #define PW(pl, cx, cy, cz) pull_w<S, R, cx, cy, cz, UNI>(pl, n)
 #define PAIR(X, Y, Z)                                  \
@@ -411,10 +414,14 @@ __global__ void __launch_bounds__(kThreads3, kMinBlocks3)
         __syncwarp();
         if (lane == 0)
 #pragma unroll
-          for (int u = 0; u < kGroup3; ++u) mbar_arrive(&empty[(j + qg + u) % kStages3]);
+          for (int u = 0; u < kGroup3; ++u) mbar_arrive(&empty[slot_of(qg + u)]);
       }
       if (stop) break;
-      j += kPairs3;
+      {
+        const unsigned e = s0 + (unsigned)kPairs3;
+        s0 = e % (unsigned)kStages3;
+        c0 += e / (unsigned)kStages3;
+      }
       if (valid) {
         R rho, ux, uy, uz, T;
         collide3(f, g, p, rho, ux, uy, uz, T);
