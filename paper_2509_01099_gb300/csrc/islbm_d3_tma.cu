@@ -32,16 +32,21 @@ constexpr int kConsumers3 = kT3X * kT3Y * kT3Z;   // one consumer thread per nod
 constexpr int kConsumerWarps3 = kConsumers3 / 32;
 constexpr int kThreads3 = kConsumers3 + 32;       // + one producer warp
 constexpr int kPairs3 = 14;
-constexpr int kStages3 = 6;
+constexpr int kStages3 = 7;
 constexpr int kGroup3 = 2;                        // pairs pulled together by the consumers
 static_assert(kPairs3 % kGroup3 == 0 && kStages3 >= 2 * kGroup3, "ring too short for a group");
 
 template <typename S>
 struct Geom3 {
   static constexpr int HX = 16 / (int)sizeof(S);
-  // a slot holds the largest pair box: halos on every axis
+  // window extents with a halo on every axis
   static constexpr int SW = kT3X + 2 * HX, SH = kT3Y + 2, SD = kT3Z + 2;
-  static constexpr unsigned SLOT = 2u * SW * SH * SD * (unsigned)sizeof(S);   // bytes per slot
+  // a slot holds the largest pair box in use: no D3Q19 / D3Q7 velocity moves
+  // along all three axes, so a box has halos on at most two
+  static constexpr unsigned XY = 2u * SW * SH * kT3Z * (unsigned)sizeof(S);
+  static constexpr unsigned XZ = 2u * SW * kT3Y * SD * (unsigned)sizeof(S);
+  static constexpr unsigned YZ = 2u * kT3X * SH * SD * (unsigned)sizeof(S);
+  static constexpr unsigned SLOT = XY > XZ ? (XY > YZ ? XY : YZ) : (XZ > YZ ? XZ : YZ);
   // ring slots, then the barriers (and the abort flag), then the packed
   // interpolation tables of the three axes when they fit
   static constexpr size_t ring_bytes() { return (size_t)kStages3 * SLOT; }
@@ -84,6 +89,16 @@ __host__ __device__ constexpr unsigned box_bytes(int type) {
          (unsigned)(kT3Y + ((type & 2) ? 2 : 0)) * (unsigned)(kT3Z + ((type & 4) ? 2 : 0)) *
          (unsigned)sizeof(S);
 }
+
+template <typename S>
+constexpr bool boxes_fit_slot() {
+  for (int q = 0; q < kPairs3; ++q)
+    if (pair_type(q) == 7 || box_bytes<S>(pair_type(q)) > Geom3<S>::SLOT) return false;
+  return true;
+}
+static_assert(boxes_fit_slot<float>() && boxes_fit_slot<__half>() &&
+                  boxes_fit_slot<__nv_bfloat16>(),
+              "every pair box fits a ring slot");
 
 // One TMA descriptor per box type (index = type bits) of the input buffer.
 struct alignas(64) Maps3 {
