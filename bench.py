@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--dim", type=int, default=2, choices=[2, 3],
                     help="2: n x n cavity (D2Q9 + D2Q5); 3: n^3 cavity (D3Q19 + D3Q7)")
-    ap.add_argument("--Ra", type=float, default=1e8)
+    ap.add_argument("--Ra", type=float, default=None,
+                    help="Rayleigh number (default: 1e8 in 2-D, 1e7 in 3-D)")
     ap.add_argument("--mesh", default="tanh", choices=["tanh", "erf", "uniform"])
     ap.add_argument("--precision", default="fp32", choices=list(BYTES_PER_VALUE))
     ap.add_argument("--no-variants", action="store_true")
@@ -74,7 +75,10 @@ def parse():
     ap.add_argument("--series-steps", type=int, default=200_000)
     ap.add_argument("--batch", action="store_true",
                     help="64-cavity Ra sweep: batched persistent launch vs a per-cavity loop")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.Ra is None:
+        args.Ra = 1e8 if args.dim == 2 else 1e7
+    return args
 
 
 def peaks():
@@ -285,7 +289,8 @@ def sweep(args, pkg, torch, flush):
     for n in (args.n, 4096):
         for mesh in ("tanh", "uniform"):
             for prec in ("fp32", "fp16dev", "bf16dev"):
-                kernels = ["direct"] if mesh == "uniform" else list(pkg.KERNELS)[1:]
+                kernels = (["direct"] if mesh == "uniform" else
+                           [k for k in list(pkg.KERNELS)[1:] if k != "tma3d"])
                 for kern in kernels:
                     s = make_solver(pkg, n, mesh, args.Ra, prec, kern)
                     steps = min(args.steps, 400 if n <= 2048 else 100)
