@@ -128,8 +128,13 @@ def profile_traffic(dim, precision, mesh, n):
             if vals.get("source_sha256") != kernel_source_sha(dim):
                 continue
             traffic = float(vals["traffic_bytes_per_launch"])
-            nodes = float(vals.get("nodes_per_launch", n ** dim))
-            return traffic * (n ** dim) / nodes
+            if path == exact:
+                return traffic
+            # another size: only a summary that states its node count (and so
+            # claims traffic in proportion to the nodes) is scaled
+            if "nodes_per_launch" not in vals:
+                continue
+            return traffic * (n ** dim) / float(vals["nodes_per_launch"])
         except Exception:
             continue
     return None
