@@ -95,9 +95,10 @@ typedef struct {
                          rows 2 stages, 4 = 8 rows 2 stages, 5 = 8 rows 3
                          stages, 6 = 16 rows 3 stages); 3-D: 7 persistent TMA
                          ring of opposite-population pairs (32x4x2 tiles, needs
-                         n_y >= 6, n_z >= 4).  2-6 in 3-D and every variant for
-                         FP64 or the upwind stencil run the direct kernel; 7 in
-                         2-D is ISLBM_ERR_ARG. */
+                         n_y >= 6, n_z >= 4); 8 / 9 z-marching columns of
+                         32x8 / 32x4 nodes with TMA rings of z levels.  2-6 in
+                         3-D and every variant for FP64 or the upwind stencil
+                         run the direct kernel; 7-9 in 2-D are ISLBM_ERR_ARG. */
   int reference;      /* reference temperature T0 of the buoyancy force and of T*
                          (Sec. 2.1): ISLBM_TREF_COLD = the cold wall (default;
                          reproduces the asymmetric centre values of Table 3),
@@ -300,7 +301,7 @@ typedef struct islbm_batch* islbm_batch_t;
  * ISLBM_KERNEL_VARIANTS entries (+inf for variants that cannot run).  Results
  * are cached per (n, mesh, a, precision) for the life of the process.
  * FP32 / FP16DEV / BF16DEV only. */
-#define ISLBM_KERNEL_VARIANTS 8
+#define ISLBM_KERNEL_VARIANTS 10
 ISLBM_API islbm_status islbm_autotune(int n, int mesh, double a, int precision, void* stream,
                                       int* best, double* us_per_step);
 
@@ -444,20 +445,26 @@ ISLBM_API islbm_status islbm_selftest_wait_timeout(void* stream);
  *     islbm_get_populations writes to the host).
  *   nx, ny: fluid nodes per axis, at least 4 each; nx*ny at most 134217728.
  *   xi_x, xi_y: device, the meshes (nx+2 and ny+2 doubles, ghost-node form as
- *     for islbm_create).
+ *     for islbm_create: strictly increasing, one lattice unit xi_1 - xi_0
+ *     shared by both axes).  The library cannot see the sizes of f, g, xi_x
+ *     and xi_y: they must hold the counts above (the Python binding checks
+ *     them before the call).
  *   Ra, Pr, opt (Ma, T_hot, T_cold; NULL = defaults): as for islbm_create.
  *   stream: cudaStream_t for the two kernels (NULL = legacy stream).
  *   out: host struct, filled on return (the call synchronises the stream).
  * Its scratch is one file-scope device array of 1 MiB (per-block partial sums
  * of at most 8192 blocks plus the result), held by every GPU that loads the
  * library until the process exits.  Every value a call reads from it is
- * written earlier in the same call.  The first call on a device looks up the
- * array's device address once (cudaGetSymbolAddress), so make that first call
- * before any stream capture.  All calls share the array: calls that overlap on
- * the GPU race, so serialise them.  Returns ISLBM_ERR_ARG (nothing launched)
- * for NULL pointers or sizes outside the limits above, ISLBM_ERR_DIVERGED if a
- * node is non-finite, ISLBM_ERR_CUDA on a launch failure; the message is
- * available from islbm_last_error(NULL). */
+ * written earlier in the same call.  Every call looks up the array's device
+ * address on the current device (cudaGetSymbolAddress) before it launches.
+ * The call synchronises its stream and copies the result to host memory, so
+ * it cannot be used inside a stream capture.  All calls share the array:
+ * calls that overlap on the GPU (e.g. on two streams) race, so serialise
+ * them.  Returns ISLBM_ERR_ARG for NULL pointers or sizes outside the limits
+ * above (nothing launched) and for meshes that are not strictly increasing or
+ * whose axes differ in lattice unit (found on the device; no result is
+ * returned), ISLBM_ERR_DIVERGED if a node is non-finite, ISLBM_ERR_CUDA on a
+ * launch failure; the message is available from islbm_last_error(NULL). */
 ISLBM_API islbm_status islbm_reduce_noalloc(const double* f, const double* g, int nx, int ny,
                                             const double* xi_x, const double* xi_y, double Ra,
                                             double Pr, const islbm_params* opt, void* stream,

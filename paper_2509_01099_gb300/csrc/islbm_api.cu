@@ -140,6 +140,35 @@ std::string encode_tensor_maps(Solver* s) {
                                      ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                      : (s->precision == ISLBM_FP16DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  if (s->dim == 3 && is_zm3d(s->variant)) {
+    // z-marching kernels: one descriptor per staging group.  Its base is the
+    // group's first plane; the dimensions are (x over the padded pitch, y, z,
+    // planes of the group[, the flow / temperature pair 19 planes apart]).
+    for (int b = 0; b < 2; ++b)
+      for (int g = 0; g < 7; ++g) {
+        unsigned bx[5];
+        const int rank = step_3d_zm_box((int)s->elem, s->variant, g, bx);
+        const bool split = step_3d_zm_split(g) != 0;
+        const cuuint64_t dims[5] = {(cuuint64_t)s->pitch, (cuuint64_t)s->n[1], (cuuint64_t)s->n[2],
+                                    (cuuint64_t)(split ? 2 : 4), 2};
+        const cuuint64_t plane_bytes = (cuuint64_t)s->plane * s->elem;
+        // R (rank 4, split): the second "plane" is the temperature rest plane
+        const cuuint64_t strides[4] = {(cuuint64_t)s->pitch * s->elem,
+                                       (cuuint64_t)s->pitch * s->n[1] * s->elem,
+                                       (split && rank == 4) ? 19 * plane_bytes : plane_bytes,
+                                       19 * plane_bytes};
+        const cuuint32_t box[5] = {bx[0], bx[1], bx[2], bx[3], bx[4]};
+        const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        void* base = static_cast<char*>(s->buf[b]) + (size_t)step_3d_zm_first_plane(g) * plane_bytes;
+        CUresult r = reinterpret_cast<EncodeFn>(fn)(
+            reinterpret_cast<CUtensorMap*>(s->tmap3[b][g]), dt, (cuuint32_t)rank, base, dims,
+            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+          return "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+      }
+    return "";
+  }
   if (s->dim == 3) {
     // 4-D view [population][z][y][x] of a buffer; a box holds a tile of two planes
     // with a halo along the axes in the bits of its type (1 x, 2 y, 4 z)
@@ -331,7 +360,8 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
   if (!(prm.Ma > 0)) return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: Ma must be positive");
   if (prm.stencil != ISLBM_STENCIL_CENTRED && prm.stencil != ISLBM_STENCIL_UPWIND)
     return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: unknown stencil");
-  if (prm.kernel < 0 || prm.kernel >= KV_COUNT || (dim == 2 && prm.kernel == KV_TMA_3D))
+  if (prm.kernel < 0 || prm.kernel >= KV_COUNT ||
+      (dim == 2 && (prm.kernel == KV_TMA_3D || is_zm3d(prm.kernel))))
     return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: unknown kernel variant");
   const double* xis[3] = {xi_x, xi_y, xi_z};
   const int ns[3] = {nx, ny, dim == 3 ? nz : 1};
@@ -447,11 +477,12 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
                      ? (precision == ISLBM_FP32 ? KV_TMA_R2S2 : KV_TMA_R4S2)
                      : KV_DIRECT;
   else
-    s->variant = s->uniform ? KV_DIRECT : KV_TMA_3D;
+    s->variant = s->uniform ? KV_DIRECT : KV_ZM3D;
   if (precision == ISLBM_FP64 || prm.stencil != ISLBM_STENCIL_CENTRED)
     s->variant = KV_DIRECT;
-  if (dim == 3 && (s->variant != KV_TMA_3D || !step_3d_tma_fits(s->n[1], s->n[2])))
+  if (dim == 3 && s->variant == KV_TMA_3D && !step_3d_tma_fits(s->n[1], s->n[2]))
     s->variant = KV_DIRECT;
+  if (dim == 3 && s->variant != KV_TMA_3D && !is_zm3d(s->variant)) s->variant = KV_DIRECT;
   s->elem = precision == ISLBM_FP64 ? 8 : (precision == ISLBM_FP32 ? 4 : 2);
   s->pitch = (s->n[0] + 31) / 32 * 32;
   s->plane = (long long)s->pitch * s->n[1] * s->n[2];
@@ -1021,8 +1052,9 @@ extern "C" islbm_status islbm_load(islbm_t s, const char* path) {
 
 extern "C" islbm_status islbm_debug_bounds(int reset, int* flagged) {
   if (!flagged) return fail(nullptr, ISLBM_ERR_ARG, "islbm_debug_bounds: NULL argument");
-  const int a = bounds_flag_d2(reset), b = bounds_flag_d3(reset);
-  if (a < 0 || b < 0) return fail(nullptr, ISLBM_ERR_CUDA, "islbm_debug_bounds: reading the flags");
-  *flagged = (a | b) ? 1 : 0;
+  const int a = bounds_flag_d2(reset), b = bounds_flag_d3(reset), c = bounds_flag_zm(reset);
+  if (a < 0 || b < 0 || c < 0)
+    return fail(nullptr, ISLBM_ERR_CUDA, "islbm_debug_bounds: reading the flags");
+  *flagged = (a | b | c) ? 1 : 0;
   return ISLBM_OK;
 }

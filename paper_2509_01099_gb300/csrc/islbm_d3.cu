@@ -452,7 +452,9 @@ struct Steady3 {
 }  // namespace
 
 cudaError_t launch_step_3d(Solver& s) {
-  cudaError_t e = s.variant == KV_TMA_3D ? launch_step_3d_tma(s) : dispatch3<Step3>(s);
+  cudaError_t e = s.variant == KV_TMA_3D  ? launch_step_3d_tma(s)
+                  : is_zm3d(s.variant)     ? launch_step_3d_zm(s)
+                                           : dispatch3<Step3>(s);
   if (e == cudaSuccess) s.cur ^= 1;
   return e;
 }

@@ -34,6 +34,7 @@ __device__ __forceinline__ bool in_window(int v, int n) {
 // reset != 0 clears them
 int bounds_flag_d2(int reset);
 int bounds_flag_d3(int reset);
+int bounds_flag_zm(int reset);
 
 // One-time launch setup of a kernel (shared-memory attribute, occupancy query),
 // run once per (kernel, current device) under a lock; *value receives what the
@@ -80,6 +81,8 @@ enum KernelVariant {
   KV_TMA_R2S3 = 5,  // persistent, TMA triple buffer, 64 x 8 tiles
   KV_TMA_R4S3 = 6,  // persistent, TMA triple buffer, 64 x 16 tiles
   KV_TMA_3D = 7,    // 3-D: persistent, warp-specialised TMA ring of population pairs
+  KV_ZM3D = 8,      // 3-D: z-marching columns of 32 x 8 nodes, TMA rings of levels
+  KV_ZM3D_T4 = 9,   // 3-D: z-marching columns of 32 x 4 nodes
   KV_COUNT
 };
 
@@ -187,6 +190,16 @@ cudaError_t launch_step_3d_tma(Solver& s);
 void step_3d_tma_box(int elem, int type, unsigned (&box)[4]);
 // whether the 3-D pipelined kernel's staged window fits the mesh
 bool step_3d_tma_fits(int ny, int nz);
+// z-marching 3-D kernels (KV_ZM3D, KV_ZM3D_T4)
+cudaError_t launch_step_3d_zm(Solver& s);
+// TMA box of staging group g (0..6) of a z-marching variant; returns the rank
+// of its descriptor (4 or 5)
+int step_3d_zm_box(int elem, int variant, int g, unsigned (&box)[5]);
+// first plane of staging group g, and whether the group is two plane pairs
+// 19 planes apart (flow and temperature) rather than consecutive planes
+int step_3d_zm_first_plane(int g);
+int step_3d_zm_split(int g);
+inline bool is_zm3d(int variant) { return variant == KV_ZM3D || variant == KV_ZM3D_T4; }
 cudaError_t launch_fields_3d(Solver& s, double* rho, double* T, double* u0, double* u1,
                              double* u2);
 cudaError_t launch_populations_3d(Solver& s, double* f, double* g);

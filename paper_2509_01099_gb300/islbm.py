@@ -19,9 +19,9 @@ LATTICES = {"d2q9_d2q5": 0, "d3q19_d3q7": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16dev": 2, "bf16dev": 3}
 STENCILS = {"centred": 0, "upwind": 1}
 REFERENCES = {"mean": 0, "cold": 1}
-KERNEL_VARIANTS = 8      # ISLBM_KERNEL_VARIANTS of include/islbm.h
+KERNEL_VARIANTS = 10     # ISLBM_KERNEL_VARIANTS of include/islbm.h
 KERNELS = {"auto": 0, "direct": 1, "tiled": 2, "tma_r4s2": 3, "tma_r2s2": 4, "tma_r2s3": 5,
-           "tma_r4s3": 6, "tma3d": 7}
+           "tma_r4s3": 6, "tma3d": 7, "zm3d": 8, "zm3d_t4": 9}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_DIVERGED",
           5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_IO"}
 
@@ -199,14 +199,43 @@ def _host(a, n):
     return arr
 
 
-def _devptr(t):
+def _check_tensor(t, n=None, name="tensor"):
+    """Type, dtype, size (at least n values) and contiguity of a float64 tensor
+    argument; None and plain ints (raw device addresses) pass unchecked."""
+    if t is None or isinstance(t, int):
+        return
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor or a device address, got {type(t).__name__}")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name}: expected float64, got {t.dtype}")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name}: needs at least {n} values, has {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+
+
+def _devptr(t, n=None, name="tensor"):
+    """Device address of a float64 CUDA tensor on the current device holding at
+    least n values (checked here: the C side trusts its sizes).  A plain int is
+    taken as a raw device address, unchecked."""
     if t is None:
         return None
     if isinstance(t, int):
         return t
     import torch
-    assert isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    _check_tensor(t, n, name)
+    if not t.is_cuda:
+        raise ValueError(f"{name}: must live in CUDA device memory")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on cuda:{t.device.index}, but the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
     return t.data_ptr()
+
+
+def _handle_nodes(h) -> int:
+    o = islbm_info(h)
+    return int(o.n[0]) * int(o.n[1]) * (int(o.n[2]) if o.dim == 3 else 1)
 
 
 def _current_stream():
@@ -283,7 +312,9 @@ def islbm_set_fields(h, T, u=None, v=None, w=None, rho=None, nodes=None):
 
 
 def islbm_set_fields_device(h, T, u=None, v=None, w=None, rho=None):
-    _check(load_library().islbm_set_fields_device(h, *[_devptr(a) for a in (rho, T, u, v, w)]), h)
+    n = _handle_nodes(h)
+    ptrs = [_devptr(a, n, k) for a, k in ((rho, "rho"), (T, "T"), (u, "u"), (v, "v"), (w, "w"))]
+    _check(load_library().islbm_set_fields_device(h, *ptrs), h)
 
 
 def islbm_set_populations(h, f, g):
@@ -307,7 +338,9 @@ def islbm_get_fields(h, shape, with_w=False):
 
 
 def islbm_get_fields_device(h, rho=None, T=None, u=None, v=None, w=None):
-    _check(load_library().islbm_get_fields_device(h, *[_devptr(a) for a in (rho, T, u, v, w)]), h)
+    n = _handle_nodes(h)
+    ptrs = [_devptr(a, n, k) for a, k in ((rho, "rho"), (T, "T"), (u, "u"), (v, "v"), (w, "w"))]
+    _check(load_library().islbm_get_fields_device(h, *ptrs), h)
 
 
 def islbm_get_populations(h, q_flow, q_temp, shape):
@@ -412,11 +445,21 @@ def islbm_reduce_noalloc(f, g, nx, ny, xi_x, xi_y, Ra, Pr=0.71, params: Params |
                          stream=None) -> dict:
     """Reductions of a 2-D state held in caller-owned device memory (torch CUDA
     float64 tensors or raw addresses); the library allocates nothing."""
+    nx, ny = int(nx), int(ny)
+    if nx < 1 or ny < 1:
+        raise ValueError(f"nx, ny must be positive, got {nx}, {ny}")
+    # the C side cannot see buffer sizes: check them (all four, then their
+    # device) before anything is launched
+    args = ((f, 9 * nx * ny, "f"), (g, 5 * nx * ny, "g"), (xi_x, nx + 2, "xi_x"),
+            (xi_y, ny + 2, "xi_y"))
+    for a in args:
+        _check_tensor(*a)
+    ptrs = tuple(_devptr(*a) for a in args)
     r = Reductions()
     if stream is None:
         stream = _current_stream()
     _check(load_library().islbm_reduce_noalloc(
-        _devptr(f), _devptr(g), int(nx), int(ny), _devptr(xi_x), _devptr(xi_y), float(Ra),
+        ptrs[0], ptrs[1], nx, ny, ptrs[2], ptrs[3], float(Ra),
         float(Pr), ctypes.byref(params) if params is not None else None, stream,
         ctypes.byref(r)))
     return {k: getattr(r, k) for k, _ in Reductions._fields_}

@@ -1,8 +1,9 @@
 """The bounds-checked build (build(debug=True), ISLBM_BOUNDS_CHECK): every
 staged shared-memory index of the pipelined kernels is checked.  Small runs of
 the 2-D TMA kernels (FP32 and FP16 storage, 8- and 16-row tiles, one cavity and
-a batch), the 3-D pipelined kernel (FP32 and BF16 storage) and a ragged 3-D box
-must leave the flag clear and give the same fields as the release build.
+a batch), the 3-D pipelined kernels (FP32, FP16 and BF16 storage; pair ring and
+z-marching columns) and ragged 3-D boxes must leave the flag clear and give
+the same fields as the release build.
 """
 import json
 import os
@@ -41,6 +42,14 @@ run("2d_fp32_r4s3", (x2, x2), "fp32", "tma_r4s3")
 x3 = pkg.islbm_mesh_tanh(37, 1.5)
 run("3d_fp32", (x3, x3, x3), "fp32", "tma3d")
 run("3d_bf16", (x3, x3, x3), "bf16dev", "tma3d")
+run("3d_zm_fp32", (x3, x3, x3), "fp32", "zm3d")
+run("3d_zm_fp16", (x3, x3, x3), "fp16dev", "zm3d")
+run("3d_zm4_bf16", (x3, x3, x3), "bf16dev", "zm3d_t4")
+unit = lambda ref, xi: xi * ((ref[1] - ref[0]) / (xi[1] - xi[0]))   # one lattice unit
+xa = pkg.islbm_mesh_tanh(41, 1.5)
+xr = (xa, unit(xa, pkg.islbm_mesh_tanh(9, 1.5)), unit(xa, pkg.islbm_mesh_tanh(13, 1.5)))
+run("3d_zm_ragged", xr, "fp32", "zm3d")
+run("3d_zm4_ragged", xr, "fp32", "zm3d_t4")
 b = pkg.Batch([dict(n=40, mesh="tanh", Ra=1e6), dict(n=72, mesh="tanh", Ra=1e7)], "fp32")
 b.step(40)
 b.synchronize()
@@ -71,8 +80,13 @@ def test_bounds_checked_build_is_clean_and_agrees():
         if name == "flagged":
             continue
         ref = release[name]
+        # the checked build may contract a product into a sum of the collision
+        # differently (one FP32 ulp); with 16-bit stochastic rounding that can
+        # flip a rounding decision of the z-marching kernels, one storage ulp
+        # that later steps carry along
+        tol = 2e-3 if name in ("3d_zm_fp16", "3d_zm4_bf16") else 1e-6
         for k, v in got.items():
             if k == "kernel":
                 assert v == ref[k]
             else:
-                assert abs(v - ref[k]) <= 1e-6 * max(abs(ref[k]), 1e-30), (name, k, v, ref[k])
+                assert abs(v - ref[k]) <= tol * max(abs(ref[k]), 1e-30), (name, k, v, ref[k])

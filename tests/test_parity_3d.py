@@ -124,8 +124,8 @@ def test_tma3d_cavity_fields_multi_tile():
     steps = 300
     ref = oracle_erf36(steps)
     xi = MESHES["erf36"]()
-    s = pkg.Solver(*xi, Ra=1e6, precision="fp32")
-    assert s.info.kernel == pkg.KERNELS["tma3d"]      # the default for stretched 3-D meshes
+    s = pkg.Solver(*xi, Ra=1e6, precision="fp32", kernel="tma3d")
+    assert s.info.kernel == pkg.KERNELS["tma3d"]
     s.set_fields(temperature_noise(s.shape, 1e-6, seed=0))
     s.step(steps)
     got = s.fields()
@@ -155,7 +155,7 @@ def test_tma3d_matches_direct_kernel_closely():
 
 def test_3d_kernel_default_choice():
     xi = O.mesh_tanh(16, 1.5)
-    cases = [((xi,) * 3, "fp32", "tma3d"), ((xi,) * 3, "bf16dev", "tma3d"),
+    cases = [((xi,) * 3, "fp32", "zm3d"), ((xi,) * 3, "bf16dev", "zm3d"),
              ((xi,) * 3, "fp64", "direct"), (MESHES["uniform11x9x7"](), "fp32", "direct")]
     for mesh, precision, kernel in cases:
         s = pkg.Solver(*mesh, Ra=1e6, precision=precision)
