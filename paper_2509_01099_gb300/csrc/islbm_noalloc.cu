@@ -7,7 +7,6 @@
 // every GPU that loads the library holds it until the process exits.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "islbm_internal.h"
 #include "islbm_store.cuh"
@@ -22,19 +21,17 @@ constexpr int kNodesPerBlock = 16384;   // nodes reduced by one block
 constexpr int kMaxBlocks = 8192;        // partial rows in the scratch array
 constexpr long long kMaxNodes = (long long)kNodesPerBlock * kMaxBlocks;   // 134,217,728
 constexpr int kRow = islbm::RED_STRIDE;  // doubles per partial row
-constexpr int kResults = 11;            // finished values written by the last kernel
-constexpr int kMaxDevices = 64;
+constexpr int kResults = 12;            // finished values written by the last kernel
 
 // 8193 rows of 16 doubles: the partials of at most kMaxBlocks blocks, then the
 // result row.  1 MiB.
 static __device__ __align__(256) double g_noalloc_scratch[(kMaxBlocks + 1) * kRow];
 
-std::mutex g_setup_mutex;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
-
 // Per-node sums of the full FP64 post-collision populations ([9][ny][nx] and
 // [5][ny][nx]), same slots as the handle's reduction.  Lattice coordinates and
-// the Eq. (18) widths come from the ghost-node meshes: W_j = (xi_{j+1} - xi_{j-1}) / (2 lu).
+// the Eq. (18) widths come from the ghost-node meshes: W_j = (xi_{j+1} - xi_{j-1}) / (2 lu),
+// with each axis's own lattice unit lu = xi_1 - xi_0 (the finish kernel rejects
+// meshes whose axes differ in it).
 __global__ void __launch_bounds__(256)
     k_noalloc_partials(const double* __restrict__ f, const double* __restrict__ g, int nx,
                        int ny, const double* __restrict__ xi_x, const double* __restrict__ xi_y,
@@ -46,9 +43,9 @@ __global__ void __launch_bounds__(256)
   const long long nodes = (long long)nx * ny;
   const long long begin = (long long)blockIdx.x * kNodesPerBlock;
   const long long end = begin + kNodesPerBlock < nodes ? begin + kNodesPerBlock : nodes;
-  const double lu = xi_x[1] - xi_x[0];
+  const double lu = xi_x[1] - xi_x[0], lu_y = xi_y[1] - xi_y[0];
   // g beta = u_f^2 / L, L the cavity height in lattice units (Table 1)
-  const double gbeta = u_f * u_f / ((xi_y[ny] - xi_y[1]) / lu + 1.0);
+  const double gbeta = u_f * u_f / ((xi_y[ny] - xi_y[1]) / lu_y + 1.0);
   const int mL = (nx % 2 == 0) ? nx / 2 - 1 : (nx - 1) / 2 - 1;
   const int mR = (nx % 2 == 0) ? nx / 2 : (nx + 1) / 2;
   const int mC = (nx % 2 == 0) ? -1 : (nx - 1) / 2;
@@ -71,7 +68,7 @@ __global__ void __launch_bounds__(256)
     const double Fy = rho * gbeta * Tr;
     const double ux = jx / rho, uy = (jy - 0.5 * Fy) / rho;
     const double wx = (xi_x[x + 2] - xi_x[x]) / (2.0 * lu);
-    const double wy = (xi_y[y + 2] - xi_y[y]) / (2.0 * lu);
+    const double wy = (xi_y[y + 2] - xi_y[y]) / (2.0 * lu_y);
     const double W = wx * wy;
     const double u2 = ux * ux + uy * uy, sp = sqrt(u2);
     acc[RED_MASS] += W * rho;
@@ -112,12 +109,21 @@ struct Phys {
 };
 
 // Fixed-order sum of the partial rows, then the finished values (Sec. 3,
-// Eq. (17), Eq. (18)) into the result row.
+// Eq. (17), Eq. (18)) into the result row.  Its last entry flags meshes that
+// islbm_create would refuse: not strictly increasing, or axes with different
+// lattice units.
 __global__ void k_noalloc_finish(double* scratch, int blocks, int nx, int ny,
                                  const double* __restrict__ xi_x, const double* __restrict__ xi_y,
                                  Phys ph) {
   using namespace islbm;
   __shared__ double sums[RED_COUNT];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j <= nx; j += blockDim.x)
+    if (!(xi_x[j + 1] > xi_x[j])) bad = 1;
+  for (int j = threadIdx.x; j <= ny; j += blockDim.x)
+    if (!(xi_y[j + 1] > xi_y[j])) bad = 1;
   const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k < RED_COUNT) {
     double v = 0.0;
@@ -130,12 +136,13 @@ __global__ void k_noalloc_finish(double* scratch, int blocks, int nx, int ny,
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  const double lu = xi_x[1] - xi_x[0];
-  auto X = [&](const double* xi, int j) { return (xi[j] - xi[0]) / lu; };
+  const double lu = xi_x[1] - xi_x[0], lu_y = xi_y[1] - xi_y[0];
+  double* res = scratch + (size_t)kMaxBlocks * kRow;
+  res[11] = (bad || !(fabs(lu_y - lu) <= 1e-9 * lu)) ? 1.0 : 0.0;
+  auto X = [&](const double* xi, int j) { return (xi[j] - xi[0]) / (xi == xi_y ? lu_y : lu); };
   const double Lx = X(xi_x, nx) - X(xi_x, 1) + 1.0;
   const double L = X(xi_y, ny) - X(xi_y, 1) + 1.0;
   const double vol = Lx * L, area = L;
-  double* res = scratch + (size_t)kMaxBlocks * kRow;
   const double sq = sqrt(ph.Ra * ph.Pr);
   res[0] = sq * sums[RED_UT] / (ph.u_f * ph.dT * vol) + 1.0;
   double q = (X(xi_x, 2) - X(xi_x, 1)) / (X(xi_x, 1) - X(xi_x, 0));
@@ -191,25 +198,20 @@ extern "C" islbm_status islbm_reduce_noalloc(const double* f, const double* g, i
   islbm_default_params(&prm);
   if (opt) prm = *opt;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
     set_last_error_static("islbm_reduce_noalloc: no usable CUDA device");
     return ISLBM_ERR_CUDA;
   }
-  double* scratch = nullptr;
-  {
-    // once per device, with that device current: the host-side name of the
-    // array is only a stand-in, the kernels need its device address
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-        set_last_error_static("islbm_reduce_noalloc: cudaGetSymbolAddress failed");
-        return ISLBM_ERR_CUDA;
-      }
-      g_scratch_ptr[dev] = static_cast<double*>(p);
-    }
-    scratch = g_scratch_ptr[dev];
+  // The host-side name of the array is only a stand-in: the kernels need its
+  // device address on the current device.  It is looked up on every call (cheap
+  // once the module is loaded), so a context created again after
+  // cudaDeviceReset, where the array may have moved, is served correctly.
+  void* sym = nullptr;
+  if (cudaGetSymbolAddress(&sym, g_noalloc_scratch) != cudaSuccess || !sym) {
+    set_last_error_static("islbm_reduce_noalloc: cudaGetSymbolAddress failed");
+    return ISLBM_ERR_CUDA;
   }
+  double* scratch = static_cast<double*>(sym);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long nodes = (long long)nx * ny;
   const int blocks = (int)((nodes + kNodesPerBlock - 1) / kNodesPerBlock);
@@ -232,6 +234,11 @@ extern "C" islbm_status islbm_reduce_noalloc(const double* f, const double* g, i
       cudaStreamSynchronize(st) != cudaSuccess) {
     set_last_error_static("islbm_reduce_noalloc: kernel launch or copy failed");
     return ISLBM_ERR_CUDA;
+  }
+  if (res[11] != 0.0) {
+    set_last_error_static(
+        "islbm_reduce_noalloc: meshes must be strictly increasing and share one lattice unit");
+    return ISLBM_ERR_ARG;
   }
   std::memset(out, 0, sizeof(*out));
   out->Nu = res[0];

@@ -101,3 +101,28 @@ def test_kernel_variant_count_matches_header():
     n = int(re.search(r"#define ISLBM_KERNEL_VARIANTS (\d+)", text).group(1))
     assert B.KERNEL_VARIANTS == n
     assert sorted(B.KERNELS.values()) == list(range(n))
+
+
+def test_noalloc_binding_rejects_bad_tensors_before_any_launch():
+    """The C side of islbm_reduce_noalloc cannot see buffer sizes: the binding
+    checks dtype, size, contiguity and device first and raises (no assert, so
+    `python -O` keeps the checks).  CPU tensors never reach the library."""
+    import torch
+    import paper_2509_01099_gb300 as pkg
+    nx = ny = 8
+    ok_f = torch.zeros(9 * nx * ny, dtype=torch.float64)
+    ok_g = torch.zeros(5 * nx * ny, dtype=torch.float64)
+    xi = torch.zeros(nx + 2, dtype=torch.float64)
+    cases = [
+        ((torch.zeros(9 * nx * ny - 1, dtype=torch.float64), ok_g, xi, xi), "f: needs at least"),
+        ((ok_f, torch.zeros(5 * nx * ny - 1, dtype=torch.float64), xi, xi), "g: needs at least"),
+        ((ok_f, ok_g, torch.zeros(nx + 1, dtype=torch.float64), xi), "xi_x: needs at least"),
+        ((ok_f, ok_g, xi, torch.zeros(ny + 1, dtype=torch.float64)), "xi_y: needs at least"),
+        ((ok_f.float(), ok_g, xi, xi), "f: expected float64"),
+        ((ok_f, ok_g, xi, xi), "must live in CUDA device memory"),
+    ]
+    for args, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            pkg.islbm_reduce_noalloc(args[0], args[1], nx, ny, args[2], args[3], 1e6, 0.71)
+    with pytest.raises(TypeError):
+        pkg.islbm_reduce_noalloc([0.0], ok_g, nx, ny, xi, xi, 1e6, 0.71)

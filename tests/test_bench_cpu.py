@@ -65,3 +65,28 @@ def test_profile_traffic_ignores_a_stale_source_hash(fake_tree):
     src = fake_tree / "paper_2509_01099_gb300" / "csrc" / bench.KERNEL_SOURCES[2][0]
     src.write_text(src.read_text() + "// edited\n")
     assert bench.profile_traffic(2, "fp32", "tanh", 1024) is None
+
+
+def test_clock_sampler_names_the_gpu_the_rank_runs_on(monkeypatch):
+    """nvidia-smi numbers physical GPUs and ignores CUDA_VISIBLE_DEVICES: the
+    sampler's selector is the device's UUID, else its PCI bus id, else the
+    visible-devices entry of the rank's local index."""
+    import torch
+
+    class Props:
+        uuid = "1234abcd-0000-1111-2222-333344445555"
+        pci_domain_id, pci_bus_id, pci_device_id = 0, 0x1B, 0
+
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda i: Props())
+    assert bench.gpu_selector(0) == "GPU-1234abcd-0000-1111-2222-333344445555"
+    Props.uuid = ""
+    assert bench.gpu_selector(0) == "00000000:1B:00.0"
+
+    def unavailable(i):
+        raise RuntimeError("no CUDA")
+
+    monkeypatch.setattr(torch.cuda, "get_device_properties", unavailable)
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "5,7")
+    assert bench.gpu_selector(1) == "7"
+    monkeypatch.delenv("CUDA_VISIBLE_DEVICES")
+    assert bench.gpu_selector(2) == "2"
