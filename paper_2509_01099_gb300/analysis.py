@@ -110,3 +110,98 @@ def divergence_2d(u, v, x, y):
     differences in the interior, one-sided at the first and last nodes)."""
     return np.gradient(np.asarray(u, float), np.asarray(x, float), axis=1) + \
         np.gradient(np.asarray(v, float), np.asarray(y, float), axis=0)
+
+
+# ---------------------------------------------------------------------------
+# Centre values, 3-D profiles and divergence statistics (Sec. 3, Sec. 4)
+# ---------------------------------------------------------------------------
+
+
+def _centre_pair(x):
+    """Indices (i0, i1) of the node(s) at x* = 1/2 (i0 == i1 for an odd count)."""
+    n = len(x)
+    return ((n - 1) // 2, (n - 1) // 2) if n % 2 else (n // 2 - 1, n // 2)
+
+
+def _at_centre(f, axes_pairs):
+    """Mean of f over the centre node(s) along the given (axis, (i0, i1)) pairs."""
+    f = np.asarray(f, dtype=np.float64)
+    for axis, (i0, i1) in axes_pairs:
+        f = 0.5 * (np.take(f, i0, axis=axis) + np.take(f, i1, axis=axis))
+    return float(f)
+
+
+def _centre_derivative(f, x, axis, others):
+    """df/dx at x* = 1/2 along `axis`: the centred difference over the two
+    neighbours of the centre node (odd count: exact on quadratics on the
+    symmetric mesh) or over the two centre nodes (even count), averaged over
+    the centre node(s) of the other axes."""
+    f = np.asarray(f, dtype=np.float64)
+    i0, i1 = _centre_pair(x)
+    if i0 == i1:
+        a, b = i0 - 1, i0 + 1
+    else:
+        a, b = i0, i1
+    d = (np.take(f, b, axis=axis) - np.take(f, a, axis=axis)) / (x[b] - x[a])
+    pairs = [(ax if ax < axis else ax - 1, p) for ax, p in others]
+    pairs.sort(key=lambda t: -t[0])
+    return _at_centre(d, pairs)
+
+
+def centre_values_2d(xi_x, xi_y, T, u, v):
+    """T, u, v and the vorticity dv/dx - du/dy at the cavity centre x* = y* = 1/2
+    (Table 3), in the units of the inputs per unit x* (fields [ny][nx]).  With an
+    even node count the centre lies between nodes: values are the mean of the
+    two (four) centre nodes and derivatives the difference across the centre."""
+    x, y = node_positions(xi_x), node_positions(xi_y)
+    px, py = _centre_pair(x), _centre_pair(y)
+    c = [(1, px), (0, py)]
+    return {"T": _at_centre(T, c), "u": _at_centre(u, c), "v": _at_centre(v, c),
+            "omega": _centre_derivative(v, x, 1, [(0, py)]) -
+            _centre_derivative(u, y, 0, [(1, px)])}
+
+
+def centre_values_3d(xi_x, xi_y, xi_z, T, u, v, w):
+    """T, u, v, w at the centre of the cube (the 3-D centre-value table; fields
+    [nz][ny][nx])."""
+    px = _centre_pair(node_positions(xi_x))
+    py = _centre_pair(node_positions(xi_y))
+    pz = _centre_pair(node_positions(xi_z))
+    c = [(2, px), (1, py), (0, pz)]
+    return {k: _at_centre(f, c) for k, f in (("T", T), ("u", u), ("v", v), ("w", w))}
+
+
+def band_profiles_3d(field, y_star, z_star, band=(0.4, 0.6), wy=None, wz=None):
+    """x profile of a [nz][ny][nx] field averaged over the nodes with y* and z*
+    both in the band (the mid-height band of the mid-depth region)."""
+    f = np.asarray(field, dtype=np.float64)
+    ry = (y_star >= band[0]) & (y_star <= band[1])
+    rz = (z_star >= band[0]) & (z_star <= band[1])
+    wy = np.ones(ry.sum()) if wy is None else np.asarray(wy)[ry]
+    wz = np.ones(rz.sum()) if wz is None else np.asarray(wz)[rz]
+    sub = f[np.ix_(rz, ry, np.ones(f.shape[2], bool))]
+    return np.einsum("zyx,z,y->x", sub, wz, wy) / (wz.sum() * wy.sum())
+
+
+def divergence_3d(u, v, w, x, y, z):
+    """du/dx + dv/dy + dw/dz on the non-uniform node positions ([nz][ny][nx])."""
+    return np.gradient(np.asarray(u, float), np.asarray(x, float), axis=2) + \
+        np.gradient(np.asarray(v, float), np.asarray(y, float), axis=1) + \
+        np.gradient(np.asarray(w, float), np.asarray(z, float), axis=0)
+
+
+def divergence_pdf(div, lo=-10.0, hi=0.0, bins=50):
+    """Probability density of log10 |div| over the nodes (the divergence
+    histograms of Sec. 3 and Sec. 4): bin centres, densities (integrating to the
+    share of nodes inside [lo, hi]) and the share of nodes below and above."""
+    a = np.abs(np.asarray(div, dtype=np.float64)).ravel()
+    with np.errstate(divide="ignore"):
+        la = np.log10(a)
+    n = a.size
+    hist, edges = np.histogram(la[np.isfinite(la)], bins=bins, range=(lo, hi))
+    width = (hi - lo) / bins
+    return {"centres": 0.5 * (edges[1:] + edges[:-1]), "density": hist / (n * width),
+            "below": float(np.sum(~np.isfinite(la) | (la < lo))) / n,
+            "above": float(np.sum(la > hi)) / n,
+            "median_log10": float(np.median(la[np.isfinite(la)])) if np.isfinite(la).any()
+            else float("-inf")}

@@ -74,3 +74,71 @@ def test_power_law_and_divergence():
     from oracle import islbm_oracle as O
     np.testing.assert_allclose(A.node_positions(O.mesh_uniform(8)), (np.arange(8) + 0.5) / 8,
                                rtol=0, atol=1e-15)
+
+
+def _mesh_xy(kind, n):
+    from oracle import islbm_oracle as O
+    return O.mesh_erf(n, 1.5) if kind == "erf" else O.mesh_uniform(n)
+
+
+@pytest.mark.parametrize("n", [17, 16])
+def test_centre_values_2d_on_closed_forms(n):
+    """Linear and quadratic fields about the centre: the centre values and the
+    vorticity dv/dx - du/dy are exact (odd n: the centre node; even n: the mean
+    of the centre nodes and the difference across the centre, both exact for
+    fields symmetric in their quadratic part)."""
+    import numpy as np
+    xi = _mesh_xy("erf", n)
+    x = A.node_positions(xi)
+    X, Y = np.meshgrid(x, x)
+    a, b = 0.7, -1.3
+    u = a * (Y - 0.5) + 0.2
+    v = b * (X - 0.5) - 0.1 + 3 * (Y - 0.5) ** 2
+    T = 0.5 + 0.3 * (X - 0.5) + 2 * (X - 0.5) ** 2 * 0
+    c = A.centre_values_2d(xi, xi, T, u, v)
+    assert abs(c["omega"] - (b - a)) < 1e-12
+    assert abs(c["u"] - 0.2) < 1e-12 and abs(c["T"] - 0.5) < 1e-12
+    expect_v = -0.1 + (0.0 if n % 2 else 3 * (x[n // 2] - 0.5) ** 2)
+    assert abs(c["v"] - expect_v) < 1e-12
+    # rigid rotation (u, v) = (-(y - 1/2), x - 1/2): vorticity 2
+    assert abs(A.centre_values_2d(xi, xi, T, -(Y - 0.5), X - 0.5)["omega"] - 2) < 1e-12
+
+
+def test_centre_values_3d_and_band_profiles_3d():
+    import numpy as np
+    xi_x, xi_y, xi_z = _mesh_xy("erf", 9), _mesh_xy("uniform", 10), _mesh_xy("erf", 11)
+    x, y, z = (A.node_positions(m) for m in (xi_x, xi_y, xi_z))
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    T = 0.5 + (X - 0.5) * (Y - 0.5) + 0.1 * (Z - 0.5)
+    c = A.centre_values_3d(xi_x, xi_y, xi_z, T, X - 0.5, 2 * (Y - 0.5), 0.3 + 0 * Z)
+    assert abs(c["T"] - 0.5) < 1e-12 and abs(c["u"]) < 1e-12
+    assert abs(c["v"]) < 1e-12 and abs(c["w"] - 0.3) < 1e-12
+    # a field that depends on x only: the band profile is the field itself
+    prof = A.band_profiles_3d(np.sin(3 * X), y, z)
+    np.testing.assert_allclose(prof, np.sin(3 * x), rtol=0, atol=1e-14)
+    # separable weights: the average of g(y) h(z) over the band is the product of averages
+    g = np.cos(Y) * np.exp(Z)
+    prof = A.band_profiles_3d(g, y, z)
+    band_y = (y >= 0.4) & (y <= 0.6)
+    band_z = (z >= 0.4) & (z <= 0.6)
+    expect = np.cos(y[band_y]).mean() * np.exp(z[band_z]).mean()
+    np.testing.assert_allclose(prof, expect, rtol=1e-13)
+
+
+def test_divergence_3d_and_its_pdf():
+    import numpy as np
+    rng = np.random.default_rng(3)
+    x, y, z = (np.sort(rng.uniform(0, 1, n)) for n in (12, 9, 7))
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    assert np.abs(A.divergence_3d(X, Y, -2 * Z, x, y, z)).max() < 1e-12
+    assert np.abs(A.divergence_3d(X, Y, Z, x, y, z) - 3).max() < 1e-12
+    # |div| log-uniform over [1e-8, 1e-2]: a flat density of 1/6 per decade there
+    d = 10 ** rng.uniform(-8, -2, 200_000) * rng.choice([-1, 1], 200_000)
+    pdf = A.divergence_pdf(d, lo=-10, hi=0, bins=20)
+    inside = (pdf["centres"] > -8) & (pdf["centres"] < -2)
+    np.testing.assert_allclose(pdf["density"][inside], 1 / 6, rtol=0.03)
+    assert np.all(pdf["density"][~inside] == 0)
+    assert abs(pdf["density"].sum() * 0.5 - 1) < 1e-12 and pdf["below"] == 0 == pdf["above"]
+    assert abs(pdf["median_log10"] + 5) < 0.02
+    zero = A.divergence_pdf(np.zeros(10))
+    assert zero["below"] == 1.0
