@@ -431,6 +431,49 @@ ISLBM_API islbm_status islbm_debug_bounds(int reset, int* flagged);
  * CUDA failure.  Synchronises `stream`; the context stays usable. */
 ISLBM_API islbm_status islbm_selftest_wait_timeout(void* stream);
 
+/* ---- 2-D slab decomposition ---------------------------------------------------
+ * The time step of Sec. 2.2 needs, at a node, the post-collision populations
+ * of its own row and of the rows next to it (the y stencil of the quadratic
+ * interpolation, or the bounce-back partner at a wall).  A cavity split into
+ * slabs of rows therefore exchanges one halo row on each side per step.  These
+ * calls let one handle per rank (each holding the whole mesh) step only its
+ * slab; the ranks move the halo rows between them (a copy, NCCL or any other
+ * transport) between steps, and combine the partial sums of the reductions.
+ * The paper runs one GPU; the split is this library's.
+ *
+ * islbm_set_row_range: subsequent islbm_step calls compute rows
+ * [row_begin, row_end) of a 2-D cavity only (0 <= row_begin < row_end <= n_y;
+ * the whole range restores the default).  Rows outside keep whatever they
+ * held; the caller must refresh rows row_begin - 1 and row_end (where they
+ * exist) from the ranks that own them before every step.  islbm_reduce then
+ * returns ISLBM_ERR_ARG: use islbm_reduce_sums and islbm_finish_sums.
+ * ISLBM_ERR_ARG for 3-D handles or an empty or out-of-mesh range. */
+ISLBM_API islbm_status islbm_set_row_range(islbm_t h, int row_begin, int row_end);
+
+/* Copy rows [row0, row0 + nrows) of the current (post-collision) state out of
+ * / into the handle: all Q_f + Q_g = 14 planes in the storage type (8, 4 or 2
+ * bytes a value), laid out [plane][row][x over the padded pitch]:
+ * 14 * nrows * pitch * bytes in all (pitch = n_x rounded up to 32, from
+ * islbm_info's bytes_per_update and n).  `dst` / `src` may be host or device
+ * memory (caller-owned).  Stream-ordered: the call returns after enqueueing the
+ * copy on the handle's stream; synchronise that stream before reading a host
+ * `dst` or reusing a host `src`.  ISLBM_ERR_ARG for 3-D handles, NULL
+ * buffers or rows outside the mesh. */
+ISLBM_API islbm_status islbm_get_rows(islbm_t h, int row0, int nrows, void* dst);
+ISLBM_API islbm_status islbm_set_rows(islbm_t h, int row0, int nrows, const void* src);
+
+/* The raw FP64 sums behind islbm_reduce over the handle's rows (all rows, or
+ * the slab of islbm_set_row_range): ISLBM_REDUCTION_SUMS doubles into the
+ * caller's host array `sums` (synchronises the stream).  Sums over disjoint
+ * slabs add up to the whole cavity's, except entry ISLBM_SUM_MAX_SLOT, a
+ * maximum.  islbm_finish_sums turns combined sums into the finished values of
+ * Sec. 3 / Sec. 4, Eq. (17), Eq. (18) (as islbm_reduce; ISLBM_ERR_DIVERGED for
+ * non-finite nodes). */
+#define ISLBM_REDUCTION_SUMS 16
+#define ISLBM_SUM_MAX_SLOT 13
+ISLBM_API islbm_status islbm_reduce_sums(islbm_t h, double* sums);
+ISLBM_API islbm_status islbm_finish_sums(islbm_t h, const double* sums, islbm_reductions* out);
+
 /* ---- reductions without allocation ------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers of
  * this library that cannot allocate device memory: code that runs while its

@@ -12,6 +12,8 @@ from .islbm import (EXPORTS, KERNEL_VARIANTS, KERNELS, LATTICES, MESH_KINDS, PRE
                     islbm_reduce_noalloc, islbm_reynolds, islbm_run_to_steady, islbm_save, islbm_selftest_wait_timeout,
                     islbm_set_fields, islbm_set_fields_device, islbm_set_populations,
                     islbm_steady_change, islbm_step, islbm_synchronize, library_path,
-                    load_library)
+                    load_library, islbm_set_row_range, islbm_get_rows, islbm_set_rows,
+                    islbm_reduce_sums, islbm_finish_sums, rows_bytes, REDUCTION_SUMS,
+                    SUM_MAX_SLOT)
 
 __all__ = [n for n in dir() if not n.startswith("_")]

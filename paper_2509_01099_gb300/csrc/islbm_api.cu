@@ -893,6 +893,10 @@ extern "C" islbm_status islbm_get_populations(islbm_t s, double* f, double* g) {
 extern "C" islbm_status islbm_reduce(islbm_t s, islbm_reductions* out) {
   NvtxRange range("islbm_reduce");
   if (!s || !out) return fail(s, ISLBM_ERR_ARG, "islbm_reduce: NULL argument");
+  if (s->row_end > 0)
+    return fail(s, ISLBM_ERR_ARG,
+                "islbm_reduce: the handle steps a slab; combine islbm_reduce_sums over the "
+                "slabs and finish them with islbm_finish_sums");
   {
     const islbm_status st = check_device_flag(s);
     if (st != ISLBM_OK) return st;
@@ -1057,4 +1061,86 @@ extern "C" islbm_status islbm_debug_bounds(int reset, int* flagged) {
     return fail(nullptr, ISLBM_ERR_CUDA, "islbm_debug_bounds: reading the flags");
   *flagged = (a | b | c) ? 1 : 0;
   return ISLBM_OK;
+}
+
+// ============================================================================
+// 2-D slab decomposition: row range, halo rows, partial sums
+// ============================================================================
+
+static_assert(RED_MAXSPEED == ISLBM_SUM_MAX_SLOT && RED_STRIDE == ISLBM_REDUCTION_SUMS,
+              "the C ABI's description of the partial sums matches the reduction slots");
+
+static void drop_graphs(Solver* s) {
+  if (s->side) cudaStreamSynchronize(s->side);
+  for (int b = 0; b < 2; ++b)
+    if (s->graph[b]) {
+      cudaGraphExecDestroy(s->graph[b]);
+      s->graph[b] = nullptr;
+    }
+}
+
+extern "C" islbm_status islbm_set_row_range(islbm_t s, int row_begin, int row_end) {
+  if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_set_row_range: NULL handle");
+  if (s->dim != 2) return fail(s, ISLBM_ERR_ARG, "islbm_set_row_range: 2-D cavities only");
+  if (row_begin < 0 || row_end > s->n[1] || row_begin >= row_end)
+    return fail(s, ISLBM_ERR_ARG, "islbm_set_row_range: need 0 <= row_begin < row_end <= n_y");
+  drop_graphs(s);   // captured steps carry the old range
+  if (row_begin == 0 && row_end == s->n[1]) {
+    s->row_begin = s->row_end = 0;
+  } else {
+    s->row_begin = row_begin;
+    s->row_end = row_end;
+  }
+  return ISLBM_OK;
+}
+
+static islbm_status rows_args(Solver* s, int row0, int nrows, const void* p, const char* name) {
+  if (!s) return fail(nullptr, ISLBM_ERR_ARG, std::string(name) + ": NULL handle");
+  if (s->dim != 2) return fail(s, ISLBM_ERR_ARG, std::string(name) + ": 2-D cavities only");
+  if (!p) return fail(s, ISLBM_ERR_ARG, std::string(name) + ": NULL buffer");
+  if (row0 < 0 || nrows <= 0 || row0 + nrows > s->n[1])
+    return fail(s, ISLBM_ERR_ARG, std::string(name) + ": rows outside the mesh");
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_get_rows(islbm_t s, int row0, int nrows, void* dst) {
+  const islbm_status st = rows_args(s, row0, nrows, dst, "islbm_get_rows");
+  if (st != ISLBM_OK) return st;
+  const size_t width = (size_t)nrows * s->pitch * s->elem;
+  const char* src = static_cast<const char*>(s->buf[s->cur]) + (size_t)row0 * s->pitch * s->elem;
+  CK(s, cudaMemcpy2DAsync(dst, width, src, (size_t)s->plane * s->elem, width, s->qf + s->qg,
+                          cudaMemcpyDefault, s->stream));
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_set_rows(islbm_t s, int row0, int nrows, const void* src) {
+  const islbm_status st = rows_args(s, row0, nrows, src, "islbm_set_rows");
+  if (st != ISLBM_OK) return st;
+  const size_t width = (size_t)nrows * s->pitch * s->elem;
+  char* dst = static_cast<char*>(s->buf[s->cur]) + (size_t)row0 * s->pitch * s->elem;
+  CK(s, cudaMemcpy2DAsync(dst, (size_t)s->plane * s->elem, src, width, width, s->qf + s->qg,
+                          cudaMemcpyDefault, s->stream));
+  s->snap_valid = false;
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_reduce_sums(islbm_t s, double* sums) {
+  NvtxRange range("islbm_reduce_sums");
+  if (!s || !sums) return fail(s, ISLBM_ERR_ARG, "islbm_reduce_sums: NULL argument");
+  {
+    const islbm_status st = check_device_flag(s);
+    if (st != ISLBM_OK) return st;
+  }
+  CK(s, launch_reduce(*s));
+  CK(s, cudaMemcpyAsync(s->hresult, s->dresult, RED_STRIDE * sizeof(double),
+                        cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  std::memcpy(sums, s->hresult, RED_STRIDE * sizeof(double));
+  return ISLBM_OK;
+}
+
+extern "C" islbm_status islbm_finish_sums(islbm_t s, const double* sums, islbm_reductions* out) {
+  if (!s || !sums || !out) return fail(s, ISLBM_ERR_ARG, "islbm_finish_sums: NULL argument");
+  std::memcpy(s->hresult, sums, RED_STRIDE * sizeof(double));
+  return finish_reductions(s, out);
 }

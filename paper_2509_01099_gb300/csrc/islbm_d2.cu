@@ -29,6 +29,7 @@ namespace {
 template <typename R>
 struct P2 {
   int nx, ny, pitch;
+  int y0, y1;           // rows the step computes: [y0, y1) (all rows unless a slab is set)
   long long plane;
   const int* bx[2];
   const R* wx[2];
@@ -192,8 +193,8 @@ __global__ void __launch_bounds__(256)
   using R = typename Store<S>::R;
   using St = Store<S>;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= p.nx || y >= p.ny) return;
+  const int y = p.y0 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+  if (x >= p.nx || y >= p.y1) return;
   const size_t idx = (size_t)y * p.pitch + x;
   const long long P = p.plane;
   // departure point behind the west / east / south / north wall
@@ -351,47 +352,85 @@ __global__ void k_pops(const S* __restrict__ s, P2<typename Store<S>::R> p, doub
   for (int i = 0; i < 5; ++i) g[i * nodes + node] = (double)Store<S>::ld(s + (9 + i) * p.plane + idx);
 }
 
-// FP64 reductions of the current state (Sec. 3): every node adds its
-// midpoint-rule weighted contributions; nodes in the planes next to the
-// isothermal walls and on the centre line add the temperature sums from
-// which the host finishes Eq. (17) and Nu_middle.
+// Population sums and velocity of one node in the compute type of the storage
+// (FP32 for FP32 / 16-bit storage, FP64 for FP64 storage): the reductions
+// accumulate in FP64, but the node's own arithmetic needs no more precision
+// than the state it reads (FP64 arithmetic runs at a small fraction of the
+// FP32 rate on this GPU).  drho, the density's deviation from 1, keeps the
+// mass accumulation free of the rounding of 1 + drho.
+template <typename R>
+struct NodeC {
+  R drho, ux, uy, T;
+};
+
+template <typename S>
+__device__ __forceinline__ NodeC<typename Store<S>::R> node_state_c(
+    const S* __restrict__ s, size_t idx, long long P, typename Store<S>::R gbeta,
+    typename Store<S>::R Ts, typename Store<S>::R Tref) {
+  using R = typename Store<S>::R;
+  R f[9], g[5];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f[i] = Store<S>::ld(s + i * P + idx);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) g[i] = Store<S>::ld(s + (9 + i) * P + idx);
+  NodeC<R> n;
+  n.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const R rho = R(1) + n.drho;
+  const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  const R jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+  const R Tr = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
+  n.T = Tr + Ts;
+  const R Fy = rho * gbeta * (n.T - Tref);
+  n.ux = jx / rho;
+  n.uy = (jy - R(0.5) * Fy) / rho;
+  return n;
+}
+
+// Reductions of the current state (Sec. 3, Eq. (17), Eq. (18)): per-block FP64
+// partial sums of the midpoint-rule weighted contributions of every node; the
+// nodes in the planes next to the isothermal walls and on the centre line add
+// the temperature sums from which the host finishes Eq. (17) and Nu_middle.
+// A block takes whole rows (of the slab when one is set), its threads the
+// columns.
 template <typename S>
 __global__ void __launch_bounds__(256)
     k_reduce(const S* __restrict__ s, P2<typename Store<S>::R> p, double gbeta, double Ts,
              double T0,
              const double* __restrict__ Wx, const double* __restrict__ Wy, double* partial) {
+  using R = typename Store<S>::R;
   double acc[RED_COUNT];
 #pragma unroll
   for (int k = 0; k < RED_COUNT; ++k) acc[k] = 0.0;
-  const long long nodes = (long long)p.nx * p.ny;
   const int mL = (p.nx % 2 == 0) ? p.nx / 2 - 1 : (p.nx - 1) / 2 - 1;  // left column of the centre pair
   const int mR = (p.nx % 2 == 0) ? p.nx / 2 : (p.nx + 1) / 2;           // right column
   const int mC = (p.nx % 2 == 0) ? -1 : (p.nx - 1) / 2;                  // centre column (odd n)
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nodes;
-       k += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(k / p.nx), x = (int)(k - (long long)y * p.nx);
-    const NodeState n = node_state(s, (size_t)y * p.pitch + x, p.plane, gbeta, Ts, T0);
-    const double W = Wx[x] * Wy[y];
-    const double u2 = n.ux * n.ux + n.uy * n.uy;
-    const double sp = sqrt(u2);
-    const double Tr = n.T - T0;
-    acc[RED_MASS] += W * n.rho;
-    acc[RED_UT] += W * n.ux * Tr;
-    acc[RED_SPEED] += W * sp;
-    acc[RED_UV2] += W * u2;
-    acc[RED_U2] += W * u2;
+  const R gb = R(gbeta), ts = R(Ts), t0 = R(T0);
+  for (int y = p.y0 + (int)blockIdx.x; y < p.y1; y += (int)gridDim.x) {
     const double wy = Wy[y];
-    if (x == 0) acc[RED_HOT1] += wy * n.T;
-    if (x == 1) acc[RED_HOT2] += wy * n.T;
-    if (x == p.nx - 1) acc[RED_COLD1] += wy * n.T;
-    if (x == p.nx - 2) acc[RED_COLD2] += wy * n.T;
-    if (x == mL) acc[RED_MIDTL] += wy * n.T;
-    if (x == mR) acc[RED_MIDTR] += wy * n.T;
-    if (mC < 0 && (x == mL || x == mR)) acc[RED_MIDCONV] += 0.5 * wy * n.ux * Tr;
-    if (x == mC) acc[RED_MIDCONV] += wy * n.ux * Tr;
-    const bool finite = isfinite(n.rho) && isfinite(n.ux) && isfinite(n.uy) && isfinite(n.T);
-    if (!finite) acc[RED_NONFINITE] += 1.0;
-    acc[RED_MAXSPEED] = fmax(acc[RED_MAXSPEED], finite ? sp : 0.0);
+    for (int x = threadIdx.x; x < p.nx; x += blockDim.x) {
+      const NodeC<R> n = node_state_c(s, (size_t)y * p.pitch + x, p.plane, gb, ts, t0);
+      const double W = Wx[x] * wy;
+      const R u2 = n.ux * n.ux + n.uy * n.uy;
+      const R sp = sqrt(u2);
+      const R uT = n.ux * (n.T - t0);
+      acc[RED_MASS] += W * (1.0 + (double)n.drho);
+      acc[RED_UT] += W * (double)uT;
+      acc[RED_SPEED] += W * (double)sp;
+      acc[RED_UV2] += W * (double)u2;
+      acc[RED_U2] += W * (double)u2;
+      const double T = (double)n.T;
+      if (x == 0) acc[RED_HOT1] += wy * T;
+      if (x == 1) acc[RED_HOT2] += wy * T;
+      if (x == p.nx - 1) acc[RED_COLD1] += wy * T;
+      if (x == p.nx - 2) acc[RED_COLD2] += wy * T;
+      if (x == mL) acc[RED_MIDTL] += wy * T;
+      if (x == mR) acc[RED_MIDTR] += wy * T;
+      if (mC < 0 && (x == mL || x == mR)) acc[RED_MIDCONV] += 0.5 * wy * (double)uT;
+      if (x == mC) acc[RED_MIDCONV] += wy * (double)uT;
+      const bool finite = isfinite(n.drho) && isfinite(n.ux) && isfinite(n.uy) && isfinite(n.T);
+      if (!finite) acc[RED_NONFINITE] += 1.0;
+      acc[RED_MAXSPEED] = fmax(acc[RED_MAXSPEED], finite ? (double)sp : 0.0);
+    }
   }
   __shared__ double sh[8][RED_COUNT];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -465,6 +504,8 @@ P2<R> make_params(const Solver& s) {
   P2<R> p;
   p.nx = s.n[0];
   p.ny = s.n[1];
+  p.y0 = s.row_end > 0 ? s.row_begin : 0;
+  p.y1 = s.row_end > 0 ? s.row_end : s.n[1];
   p.pitch = s.pitch;
   p.plane = s.plane;
   for (int k = 0; k < 2; ++k) {
@@ -492,6 +533,9 @@ P2<R> make_params(const Solver& s) {
   p.step = (unsigned)s.time;
   return p;
 }
+
+// rows of the step: the slab [row_begin, row_end) when one is set
+int step_rows(const Solver& s) { return s.row_end > 0 ? s.row_end - s.row_begin : s.n[1]; }
 
 
 // ---------------------------------------------------------------------------
@@ -633,7 +677,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ sm, const float4
     for (int m = 0; m < R; ++m) {
       const int y = yr0 + m;
       const int lr = y - ry0;
-      if (y >= p.ny) {
+      if (y >= p.y1) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i][m] = 0.f;
 #pragma unroll
@@ -678,7 +722,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ sm, const float4
 #pragma unroll
   for (int m = 0; m < R; m += 2) {
     const int y = yr0 + m;
-    if (y >= p.ny) break;
+    if (y >= p.y1) break;
     float2 fn[9], gn[5];
 #pragma unroll
     for (int i = 0; i < 9; ++i) fn[i] = make_float2(f[i][m], f[i][m + 1]);
@@ -694,7 +738,7 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ sm, const float4
 #pragma unroll
     for (int i = 0; i < 5; ++i)
       Store<S>::st_sr(fout + (size_t)(9 + i) * p.plane + idx, gn[i].x, sr_next(r));
-    if (y + 1 < p.ny) {
+    if (y + 1 < p.y1) {
       const size_t idx1 = idx + p.pitch;
       unsigned r1 = sr_seed(idx1, p.step);
 #pragma unroll
@@ -716,7 +760,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   S* sm = reinterpret_cast<S*>(smem_raw);
   float4* wyt = reinterpret_cast<float4*>(smem_raw + (size_t)14 * G::PLANE * sizeof(S));
 
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
+  const int x0 = blockIdx.x * kTX, y0 = p.y0 + (int)blockIdx.y * TY;
   const int cx0 = x0 - HX;
   const int ry0 = max(0, min(y0 - 1, p.ny - 3));
   // ---- stage the tile + halo of every plane ----
@@ -793,13 +837,13 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)STAGES * ST::BYTES);
   __shared__ int tile_of[STAGES];   // claimed tile of each stage (dynamic order)
-  const int ntx = (p.nx + kTX - 1) / kTX, nty = (p.ny + TY - 1) / TY;
+  const int ntx = (p.nx + kTX - 1) / kTX, nty = (p.y1 - p.y0 + TY - 1) / TY;
   const int ntiles = ntx * nty;
   const int stride = STAGES * (int)gridDim.x;
   auto tile_origin = [&](int t, int& x0, int& y0, int& ry0) {
     const int ty = t / ntx;
     x0 = (t - ty * ntx) * kTX;
-    y0 = ty * TY;
+    y0 = p.y0 + ty * TY;
     ry0 = max(0, min(y0 - 1, p.ny - 3));
   };
   auto tables = [&](int st) {
@@ -975,7 +1019,7 @@ cudaError_t launch_tiled(const Solver& s, const S* in, S* out, const P2<float>& 
       },
       nullptr);
   if (e != cudaSuccess) return e;
-  const dim3 grid((s.n[0] + kTX - 1) / kTX, (s.n[1] + G::TY - 1) / G::TY);
+  const dim3 grid((s.n[0] + kTX - 1) / kTX, (step_rows(s) + G::TY - 1) / G::TY);
   k_step_tiled<S, R, UNI><<<grid, kThreads, G::smem_bytes(), s.stream>>>(in, out, p);
   return cudaGetLastError();
 }
@@ -1003,7 +1047,7 @@ cudaError_t launch_tma(const Solver& s, int cur, S* out, const P2<float>& p) {
       &blocks_per_sm);
   if (e != cudaSuccess) return e;
   if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int ntiles = ((s.n[0] + kTX - 1) / kTX) * ((s.n[1] + G::TY - 1) / G::TY);
+  const int ntiles = ((s.n[0] + kTX - 1) / kTX) * ((step_rows(s) + G::TY - 1) / G::TY);
   const int grid = std::min(ntiles, s.sm_count * blocks_per_sm);
   // claimed tiles pay off once a CTA walks more than a few dozen tiles
   const int dynamic = ntiles >= kDynamicTilesPerCta * grid ? 1 : 0;
@@ -1014,6 +1058,7 @@ cudaError_t launch_tma(const Solver& s, int cur, S* out, const P2<float>& p) {
 
 dim3 block2() { return dim3(32, 8); }
 dim3 grid2(const Solver& s) { return dim3((s.n[0] + 31) / 32, (s.n[1] + 7) / 8); }
+dim3 grid2_step(const Solver& s) { return dim3((s.n[0] + 31) / 32, (step_rows(s) + 7) / 8); }
 
 // Dispatch on the storage type.
 template <template <typename> class Fn, typename... A>
@@ -1049,9 +1094,9 @@ struct StepFn {
       }
     }
     if (s.uniform)
-      k_step<S, true><<<grid2(s), block2(), 0, s.stream>>>(in, out, p);
+      k_step<S, true><<<grid2_step(s), block2(), 0, s.stream>>>(in, out, p);
     else
-      k_step<S, false><<<grid2(s), block2(), 0, s.stream>>>(in, out, p);
+      k_step<S, false><<<grid2_step(s), block2(), 0, s.stream>>>(in, out, p);
     return cudaGetLastError();
   }
 };

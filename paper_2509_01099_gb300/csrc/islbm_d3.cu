@@ -262,43 +262,85 @@ __global__ void k_pops3(const S* __restrict__ s, P3<typename Store<S>::R> p, dou
   for (int i = 0; i < 7; ++i) g[i * nodes + node] = (double)Store<S>::ld(s + (19 + i) * p.plane + idx);
 }
 
-// FP64 reductions (Sec. 4): volume sums and the wall-plane temperature sums of
-// Eq. (17) with the wall-plane weights W_y W_z.
+// Population sums and velocity of one node in the compute type of the storage
+// (as the 2-D node_state_c): FP64 accumulation, arithmetic at the state's own
+// precision.
+template <typename R>
+struct NodeC3 {
+  R drho, ux, uy, uz, T;
+};
+
+template <typename S>
+__device__ __forceinline__ NodeC3<typename Store<S>::R> node_state3_c(
+    const S* __restrict__ s, size_t idx, long long P, typename Store<S>::R gbeta,
+    typename Store<S>::R Ts, typename Store<S>::R Tref) {
+  using R = typename Store<S>::R;
+  R f[19], g[7];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) f[i] = Store<S>::ld(s + i * P + idx);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) g[i] = Store<S>::ld(s + (19 + i) * P + idx);
+  R drho = 0, jx = 0, jy = 0, jz = 0, Tr = 0;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    drho += f[i];
+    jx += R(kE3[i][0]) * f[i];
+    jy += R(kE3[i][1]) * f[i];
+    jz += R(kE3[i][2]) * f[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 7; ++i) Tr += g[i];
+  NodeC3<R> n;
+  n.drho = drho;
+  const R rho = R(1) + drho;
+  n.T = Tr + Ts;
+  const R Fy = rho * gbeta * (n.T - Tref);
+  n.ux = jx / rho;
+  n.uy = (jy - R(0.5) * Fy) / rho;
+  n.uz = jz / rho;
+  return n;
+}
+
+// Reductions (Sec. 4): FP64 volume sums and the wall-plane temperature sums of
+// Eq. (17) with the wall-plane weights W_y W_z.  A block takes whole rows
+// (y, z), its threads the columns.
 template <typename S>
 __global__ void __launch_bounds__(256)
     k_reduce3(const S* __restrict__ s, P3<typename Store<S>::R> p, double gbeta, double Ts,
               double T0,
               const double* __restrict__ Wx, const double* __restrict__ Wy,
               const double* __restrict__ Wz, double* partial) {
+  using R = typename Store<S>::R;
   double acc[RED_COUNT];
 #pragma unroll
   for (int k = 0; k < RED_COUNT; ++k) acc[k] = 0.0;
-  const long long nodes = (long long)p.nx * p.ny * p.nz;
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nodes;
-       k += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(k % p.nx);
-    const long long r = k / p.nx;
-    const int y = (int)(r % p.ny), z = (int)(r / p.ny);
-    const NodeState3 n =
-        node_state3(s, ((size_t)z * p.ny + y) * p.pitch + x, p.plane, gbeta, Ts, T0);
+  const int rows = p.ny * p.nz;
+  const R gb = R(gbeta), ts = R(Ts), t0 = R(T0);
+  for (int row = (int)blockIdx.x; row < rows; row += (int)gridDim.x) {
+    const int z = row / p.ny, y = row - z * p.ny;
     const double wp = Wy[y] * Wz[z];
-    const double W = Wx[x] * wp;
-    const double u2 = n.ux * n.ux + n.uy * n.uy + n.uz * n.uz;
-    const double sp = sqrt(u2);
-    const double Tr = n.T - T0;
-    acc[RED_MASS] += W * n.rho;
-    acc[RED_UT] += W * n.ux * Tr;
-    acc[RED_SPEED] += W * sp;
-    acc[RED_UV2] += W * (n.ux * n.ux + n.uy * n.uy);
-    acc[RED_U2] += W * u2;
-    if (x == 0) acc[RED_HOT1] += wp * n.T;
-    if (x == 1) acc[RED_HOT2] += wp * n.T;
-    if (x == p.nx - 1) acc[RED_COLD1] += wp * n.T;
-    if (x == p.nx - 2) acc[RED_COLD2] += wp * n.T;
-    const bool finite = isfinite(n.rho) && isfinite(n.ux) && isfinite(n.uy) && isfinite(n.uz) &&
-                        isfinite(n.T);
-    if (!finite) acc[RED_NONFINITE] += 1.0;
-    acc[RED_MAXSPEED] = fmax(acc[RED_MAXSPEED], finite ? sp : 0.0);
+    const size_t base = ((size_t)z * p.ny + y) * p.pitch;
+    for (int x = threadIdx.x; x < p.nx; x += blockDim.x) {
+      const NodeC3<R> n = node_state3_c(s, base + x, p.plane, gb, ts, t0);
+      const double W = Wx[x] * wp;
+      const R uv2 = n.ux * n.ux + n.uy * n.uy;
+      const R u2 = uv2 + n.uz * n.uz;
+      const R sp = sqrt(u2);
+      acc[RED_MASS] += W * (1.0 + (double)n.drho);
+      acc[RED_UT] += W * (double)(n.ux * (n.T - t0));
+      acc[RED_SPEED] += W * (double)sp;
+      acc[RED_UV2] += W * (double)uv2;
+      acc[RED_U2] += W * (double)u2;
+      const double T = (double)n.T;
+      if (x == 0) acc[RED_HOT1] += wp * T;
+      if (x == 1) acc[RED_HOT2] += wp * T;
+      if (x == p.nx - 1) acc[RED_COLD1] += wp * T;
+      if (x == p.nx - 2) acc[RED_COLD2] += wp * T;
+      const bool finite = isfinite(n.drho) && isfinite(n.ux) && isfinite(n.uy) &&
+                          isfinite(n.uz) && isfinite(n.T);
+      if (!finite) acc[RED_NONFINITE] += 1.0;
+      acc[RED_MAXSPEED] = fmax(acc[RED_MAXSPEED], finite ? (double)sp : 0.0);
+    }
   }
   __shared__ double sh[8][RED_COUNT];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

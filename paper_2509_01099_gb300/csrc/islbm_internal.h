@@ -148,6 +148,9 @@ struct Solver {
   std::string err;
   unsigned long long fingerprint = 0;
   int variant = KV_DIRECT;        // step kernel of the 2-D FP32/16-bit path
+  // 2-D slab of a domain decomposition: steps and reductions cover rows
+  // [row_begin, row_end) only (row_end == 0: every row)
+  int row_begin = 0, row_end = 0;
   int sm_count = 0;
   // device words of the pipelined kernels: [0] error flag, [1] tiles claimed,
   // [2] CTAs finished (the 2-D TMA kernel's dynamic schedule; zero between launches)

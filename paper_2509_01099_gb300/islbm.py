@@ -40,8 +40,11 @@ EXPORTS = (
     "islbm_cnn_gemm_bf16", "islbm_cnn_im2col", "islbm_cnn_col2im",
     "islbm_cnn_upsample2x", "islbm_cnn_tanh", "islbm_cnn_tanh_back", "islbm_cnn_to_bf16",
     "islbm_cnn_colsum", "islbm_cnn_mse", "islbm_cnn_adam", "islbm_cnn_pack_fields",
-    "islbm_cnn_unpack_fields",
+    "islbm_cnn_unpack_fields", "islbm_set_row_range", "islbm_get_rows", "islbm_set_rows",
+    "islbm_reduce_sums", "islbm_finish_sums",
 )
+REDUCTION_SUMS = 16     # ISLBM_REDUCTION_SUMS of include/islbm.h
+SUM_MAX_SLOT = 13       # ISLBM_SUM_MAX_SLOT: the one partial combined by max
 MESH_KINDS = {"uniform": 0, "erf": 1, "tanh": 2}
 
 
@@ -167,6 +170,11 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
                                ctypes.c_longlong, vp]),
         "islbm_run_to_steady": (i, [h, d, ctypes.c_longlong, ctypes.c_longlong,
                                     P(ctypes.c_longlong), dp, dp]),
+        "islbm_set_row_range": (i, [h, i, i]),
+        "islbm_get_rows": (i, [h, i, i, vp]),
+        "islbm_set_rows": (i, [h, i, i, vp]),
+        "islbm_reduce_sums": (i, [h, dp]),
+        "islbm_finish_sums": (i, [h, dp, P(Reductions)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -327,11 +335,20 @@ def islbm_step(h, n: int = 1):
     _check(load_library().islbm_step(h, int(n)), h)
 
 
-def islbm_get_fields(h, shape, with_w=False):
+def islbm_get_fields(h, shape, with_w=False, out=None):
+    """Fields into new arrays, or into `out` (a dict of caller-owned contiguous
+    float64 host arrays with the keys rho, T, u, v[, w], e.g. pinned memory)."""
     nodes = int(np.prod(shape))
-    out = {k: np.empty(nodes) for k in ("rho", "T", "u", "v")}
-    if with_w:
-        out["w"] = np.empty(nodes)
+    keys = ("rho", "T", "u", "v") + (("w",) if with_w else ())
+    if out is None:
+        out = {k: np.empty(nodes) for k in keys}
+    flat = {}
+    for k in keys:
+        a = out[k]
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != nodes:
+            raise ValueError(f"{k}: expected a contiguous float64 array of {nodes} values")
+        flat[k] = a.reshape(-1)
+    out = flat
     _check(load_library().islbm_get_fields(h, _dptr(out["rho"]), _dptr(out["T"]), _dptr(out["u"]),
                                            _dptr(out["v"]), _dptr(out.get("w"))), h)
     return {k: a.reshape(shape) for k, a in out.items()}
@@ -354,6 +371,72 @@ def islbm_get_populations(h, q_flow, q_temp, shape):
 def islbm_reduce(h, check: bool = True) -> dict:
     r = Reductions()
     st = load_library().islbm_reduce(h, ctypes.byref(r))
+    if check:
+        _check(st, h)
+    out = {k: getattr(r, k) for k, _ in Reductions._fields_}
+    out["status"] = st
+    return out
+
+
+def islbm_set_row_range(h, row_begin: int, row_end: int):
+    _check(load_library().islbm_set_row_range(h, int(row_begin), int(row_end)), h)
+
+
+def _rows_buffer(buf, nbytes, name):
+    """Address of a caller buffer of at least nbytes: a contiguous torch tensor
+    (host or CUDA device) or numpy array."""
+    try:
+        import torch
+        if isinstance(buf, torch.Tensor):
+            if not buf.is_contiguous():
+                raise ValueError(f"{name}: must be contiguous")
+            if buf.numel() * buf.element_size() < nbytes:
+                raise ValueError(f"{name}: needs {nbytes} bytes, has "
+                                 f"{buf.numel() * buf.element_size()}")
+            if buf.is_cuda and buf.device.index != torch.cuda.current_device():
+                raise ValueError(f"{name}: not on the current device")
+            return buf.data_ptr()
+    except ImportError:
+        pass
+    if isinstance(buf, np.ndarray):
+        if not buf.flags.c_contiguous:
+            raise ValueError(f"{name}: must be C-contiguous")
+        if buf.nbytes < nbytes:
+            raise ValueError(f"{name}: needs {nbytes} bytes, has {buf.nbytes}")
+        return buf.ctypes.data
+    raise TypeError(f"{name}: expected a torch tensor or a numpy array")
+
+
+def rows_bytes(h, nrows: int) -> int:
+    """Bytes of islbm_get_rows / islbm_set_rows for nrows rows of handle h."""
+    o = islbm_info(h)
+    elem = int(round(o.bytes_per_update / (2 * (o.q_flow + o.q_temp))))
+    pitch = (int(o.n[0]) + 31) // 32 * 32
+    return (o.q_flow + o.q_temp) * int(nrows) * pitch * elem
+
+
+def islbm_get_rows(h, row0: int, nrows: int, dst):
+    ptr = _rows_buffer(dst, rows_bytes(h, nrows), "dst")
+    _check(load_library().islbm_get_rows(h, int(row0), int(nrows), ptr), h)
+
+
+def islbm_set_rows(h, row0: int, nrows: int, src):
+    ptr = _rows_buffer(src, rows_bytes(h, nrows), "src")
+    _check(load_library().islbm_set_rows(h, int(row0), int(nrows), ptr), h)
+
+
+def islbm_reduce_sums(h) -> np.ndarray:
+    sums = np.zeros(REDUCTION_SUMS)
+    _check(load_library().islbm_reduce_sums(h, _dptr(sums)), h)
+    return sums
+
+
+def islbm_finish_sums(h, sums, check: bool = True) -> dict:
+    sums = np.ascontiguousarray(sums, dtype=np.float64)
+    if sums.size != REDUCTION_SUMS:
+        raise ValueError(f"expected {REDUCTION_SUMS} sums, got {sums.size}")
+    r = Reductions()
+    st = load_library().islbm_finish_sums(h, _dptr(sums), ctypes.byref(r))
     if check:
         _check(st, h)
     out = {k: getattr(r, k) for k, _ in Reductions._fields_}
@@ -607,8 +690,8 @@ class Solver:
     def step(self, n: int = 1):
         islbm_step(self.h, n)
 
-    def fields(self) -> dict:
-        return islbm_get_fields(self.h, self.shape, with_w=self.dim == 3)
+    def fields(self, out=None) -> dict:
+        return islbm_get_fields(self.h, self.shape, with_w=self.dim == 3, out=out)
 
     def fields_device(self, rho=None, T=None, u=None, v=None, w=None):
         islbm_get_fields_device(self.h, rho, T, u, v, w)
@@ -639,6 +722,25 @@ class Solver:
 
     def save(self, path):
         islbm_save(self.h, path)
+
+    # ---- slab of a 2-D domain decomposition (paper_2509_01099_gb300.decomp) ----
+    def set_row_range(self, row_begin: int, row_end: int):
+        islbm_set_row_range(self.h, row_begin, row_end)
+
+    def rows_bytes(self, nrows: int) -> int:
+        return rows_bytes(self.h, nrows)
+
+    def get_rows(self, row0: int, nrows: int, dst):
+        islbm_get_rows(self.h, row0, nrows, dst)
+
+    def set_rows(self, row0: int, nrows: int, src):
+        islbm_set_rows(self.h, row0, nrows, src)
+
+    def reduce_sums(self) -> np.ndarray:
+        return islbm_reduce_sums(self.h)
+
+    def finish_sums(self, sums, check: bool = True) -> dict:
+        return islbm_finish_sums(self.h, sums, check)
 
     def load(self, path):
         islbm_load(self.h, path)
