@@ -73,6 +73,12 @@ def parse():
     ap.add_argument("--series", action="store_true",
                     help="1024^2 Ra=1e8 for --series-steps steps with Nu every 1000 steps")
     ap.add_argument("--series-steps", type=int, default=200_000)
+    ap.add_argument("--grid-study", action="store_true",
+                    help="steady runs on a sequence of erf meshes (--grids, --dim, --Ra), each "
+                         "started from the previous one's steady state; observed orders, "
+                         "extrapolated values and GCI beside the paper's tables")
+    ap.add_argument("--grids", default="513,1025,2049",
+                    help="mesh sizes of --grid-study, coarse to fine")
     ap.add_argument("--batch", action="store_true",
                     help="64-cavity Ra sweep: batched persistent launch vs a per-cavity loop")
     args = ap.parse_args()
@@ -90,7 +96,7 @@ def peaks():
 
 KERNEL_SOURCES = {
     2: ("islbm_d2.cu", "islbm_lanes.cuh", "islbm_store.cuh", "islbm_tma.cuh"),
-    3: ("islbm_d3_tma.cu", "islbm_d3_common.cuh", "islbm_lanes.cuh", "islbm_store.cuh",
+    3: ("islbm_d3_zm.cu", "islbm_d3_common.cuh", "islbm_lanes.cuh", "islbm_store.cuh",
         "islbm_tma.cuh"),
 }
 
@@ -140,14 +146,33 @@ def profile_traffic(dim, precision, mesh, n):
     return None
 
 
+def gpu_selector(local: int) -> str:
+    """nvidia-smi -i argument of the GPU this rank runs on.  nvidia-smi numbers
+    the physical GPUs and ignores CUDA_VISIBLE_DEVICES, so the device is named
+    by its UUID (else its PCI bus id, else the visible-devices entry)."""
+    try:
+        import torch
+        pr = torch.cuda.get_device_properties(local)
+        uuid = str(getattr(pr, "uuid", "") or "")
+        if uuid:
+            return uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        if hasattr(pr, "pci_bus_id"):
+            return "%08X:%02X:%02X.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+    except Exception:
+        pass
+    vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    return vis[local] if local < len(vis) else str(local)
+
+
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region,
+    of the GPU named by `index` (an nvidia-smi -i selector: UUID, PCI bus id or index)."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index):
         self.index = index
         self.proc = None
         self.lines = []
@@ -192,32 +217,79 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+                "reasons": sorted(reasons), "gpu": str(self.index)}
 
 
-def cpu_baseline(n: int, steps: int, mesh: str):
-    """FP64 numpy oracle on the host cores (one thread), a bounded sample of the workload."""
-    code = f"""
+_ORACLE_SAMPLE = """
 import os, sys, time, json
-sys.path.insert(0, {ROOT!r})
+sys.path.insert(0, {root!r})
 from oracle import islbm_oracle as O
 from synthetic import temperature_noise
 xi = getattr(O, 'mesh_{mesh}')({n}, 1.5) if '{mesh}' != 'uniform' else O.mesh_uniform({n})
 cav = O.Cavity(xi, xi, params=O.Params(Ra=1e8))
-cav.init_fields(temperature_noise(cav.shape, 1e-6, seed=0))
+cav.init_fields(temperature_noise(cav.shape, 1e-6, seed={seed}))
 cav.step(1)
 t = time.perf_counter(); cav.step({steps}); dt = time.perf_counter() - t
 print(json.dumps({{"seconds": dt}}))
 """
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(n: int, steps: int, mesh: str):
+    """The FP64 numpy oracle on the host cores, a bounded sample of the workload:
+    `steps` time steps of the n x n cavity, once on one core, then as one
+    independent cavity per core on every core at once (separate processes, one
+    BLAS thread each); the all-core rate is the headline value."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=900)
-    if r.returncode != 0:
-        return {"error": r.stderr[-300:]}
-    sec = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
-    return {"value": n * n * steps / (sec * 1e6), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+    cores = os.cpu_count() or 1
+
+    def launch(seed):
+        code = _ORACLE_SAMPLE.format(root=ROOT, mesh=mesh, n=n, seed=seed, steps=steps)
+        return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                                stderr=subprocess.PIPE, text=True, env=env)
+
+    def seconds(proc):
+        out, err = proc.communicate(timeout=900)
+        if proc.returncode != 0:
+            raise RuntimeError(err[-300:])
+        return json.loads(out.strip().splitlines()[-1])["seconds"]
+
+    try:
+        sec1 = seconds(launch(0))
+        t0 = time.perf_counter()
+        procs = [launch(k) for k in range(cores)]
+        secs = [seconds(p) for p in procs]
+        wall = time.perf_counter() - t0
+    except Exception as e:   # noqa: BLE001 - reported, not raised
+        return {"error": str(e)[-300:]}
+    one = n * n * steps / (sec1 * 1e6)
+    # aggregate: every core's cavity steps over the slowest core's timed loop
+    allc = cores * n * n * steps / (max(secs) * 1e6)
+    model = cpu_model()
+    return {"value": allc, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"{steps} time steps of the {n}x{n} {mesh} cavity (Ra=1e8) by the FP64 "
-                      f"numpy oracle on one host core ({sec:.1f} s)"}
+                      f"numpy oracle, one independent cavity per core on all {cores} cores "
+                      f"({model}); slowest core {max(secs):.1f} s, all processes {wall:.1f} s",
+            "cpu_model": model,
+            "single_core": {"value": one, "unit": "MLUPS", "cores": 1,
+                            "sample": f"the same sample on one core ({sec1:.1f} s)"}}
 
 
 def dist_setup(args):
@@ -247,27 +319,35 @@ def max_over_ranks(world, x: float) -> float:
 
 
 def run_reference(args, world, rank):
-    """Reference arm: the FP64 oracle on the host cores, each step a bounded sample
-    (one time step of a 128 x 128 cavity with the workload's mesh and Ra)."""
+    """Reference arm: the FP64 oracle on one host core, each step one time step of
+    the workload itself (the n x n cavity with its mesh and Ra; a 3-D workload
+    is sampled on a 48^3 cube: the oracle needs ~20 s per step at 256^3)."""
     if rank != 0:
         return
+    # one core: numpy's BLAS reads its thread count when it is first imported
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
     from oracle import islbm_oracle as O
     from synthetic import temperature_noise
-    n = 128
+    n = args.n if args.dim == 2 else 48
     xi = O.mesh_uniform(n) if args.mesh == "uniform" else getattr(O, "mesh_" + args.mesh)(n, 1.5)
-    cav = O.Cavity(xi, xi, params=O.Params(Ra=args.Ra))
+    cav = O.Cavity(*([xi] * args.dim), params=O.Params(Ra=args.Ra))
     cav.init_fields(temperature_noise(cav.shape, 1e-6, seed=0))
     cav.step(max(3, args.warmup))
     t = time.perf_counter()
     cav.step(args.steps)
     sec = time.perf_counter() - t
-    value = n * n * args.steps / (sec * 1e6)
-    sample = f"{args.steps} time steps of a {n}x{n} {args.mesh} cavity (Ra={args.Ra:g}) by the FP64 numpy oracle"
+    value = n ** args.dim * args.steps / (sec * 1e6)
+    shape = "x".join([str(n)] * args.dim)
+    sample = (f"{args.steps} time steps of the {shape} {args.mesh} cavity (Ra={args.Ra:g}) by the "
+              f"FP64 numpy oracle on one core")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": sample},
+            "config": {"workload": WORKLOAD if (args.dim == 2 and args.n == 1024 and
+                                                args.mesh == "tanh") else shape + " cavity",
+                       "sample": sample},
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
@@ -285,7 +365,9 @@ KERNEL_NAMES = {1: "k_step / k_step3 (direct: one thread per node, interpolation
                 2: "k_step_tiled (cp.async tile staging)",
                 3: "k_step_tma<S,4,2>", 4: "k_step_tma<S,2,2>", 5: "k_step_tma<S,2,3>",
                 6: "k_step_tma<S,4,3>",
-                7: "k_step3_tma (3-D: warp-specialised TMA ring of population pairs)"}
+                7: "k_step3_tma (3-D: warp-specialised TMA ring of population pairs)",
+                8: "k_step3_zm<S,8> (3-D: z-marching 32x8 columns, TMA rings of levels)",
+                9: "k_step3_zm<S,4> (3-D: z-marching 32x4 columns, TMA rings of levels)"}
 
 
 def sweep(args, pkg, torch, flush):
@@ -342,23 +424,23 @@ def steady(args, pkg, torch):
                       "arms": res}), flush=True)
 
 
-def batch(args, pkg, torch):
+def batch_measure(pkg, torch, K=640, warm=128):
     """The batched sweep: 64 2-D cavities, Ra log-uniform in [1e6, 1e8] and
     N from {128, 256, 384, 512} (PCG64 seed 0), tanh meshes (a = 1.5), FP32,
     tile shapes from the autotuner.  Device time of K steps of the whole batch
     (one persistent launch per tile shape and step, replayed from CUDA graphs)
-    against the same cavities advanced one after the other."""
+    against the same cavities advanced one after the other, K steps each, also
+    timed (CUDA events around the whole sequential loop)."""
     from synthetic import ra_sweep, temperature_noise
     ra, ns = ra_sweep(64, seed=0)
     cavs = [dict(n=int(n), mesh="tanh", a=1.5, Ra=float(r)) for r, n in zip(ra, ns)]
     nodes = sum(c["n"] ** 2 for c in cavities_sorted(cavs))
-    K = 640
     t0 = time.perf_counter()
     b = pkg.Batch(cavs, precision="fp32", autotune=True)
     t_setup = time.perf_counter() - t0
     for k, m in enumerate(b.members):
         m.set_fields(temperature_noise(m.shape, 1e-6, seed=k))
-    b.step(128)
+    b.step(warm)
     b.synchronize()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -367,7 +449,10 @@ def batch(args, pkg, torch):
     e1.record(stream)
     b.synchronize()
     t_batch = e0.elapsed_time(e1) / 1e3
-    rows = sorted(set(b.tile_rows(k) for k in range(len(cavs))))
+    rows = {}
+    for k, c in enumerate(cavs):
+        rows.setdefault(str(c["n"]), set()).add(b.tile_rows(k))
+    rows = {n: sorted(v) for n, v in sorted(rows.items(), key=lambda t: int(t[0]))}
     b.close()
     # the same cavities, one solver after the other (each with its default kernel)
     solvers = []
@@ -375,7 +460,7 @@ def batch(args, pkg, torch):
         xi = pkg.islbm_mesh_tanh(c["n"], 1.5)
         s = pkg.Solver(xi, xi, Ra=c["Ra"], precision="fp32")
         s.set_fields(temperature_noise(s.shape, 1e-6, seed=k))
-        s.step(128)
+        s.step(warm)
         solvers.append(s)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -386,12 +471,33 @@ def batch(args, pkg, torch):
     t_seq = e0.elapsed_time(e1) / 1e3
     for s in solvers:
         s.close()
-    print(json.dumps({"batch": True, "cavities": len(cavs), "nodes": nodes, "steps": K,
-                      "MLUPS_batched": nodes * K / (t_batch * 1e6),
-                      "MLUPS_sequential": nodes * K / (t_seq * 1e6),
-                      "speedup": t_seq / t_batch, "tile_rows_used": rows,
-                      "setup_s_with_autotune": t_setup,
-                      "GBps_batched": 112 * nodes * K / t_batch / 1e9}), flush=True)
+    peak = (peaks() or {}).get("hbm_gbs", 6800.0)
+    return {"cavities": len(cavs), "nodes": nodes, "steps": K,
+            "MLUPS": nodes * K / (t_batch * 1e6),
+            "MLUPS_sequential_timed": nodes * K / (t_seq * 1e6),
+            "speedup_over_sequential": t_seq / t_batch, "tile_rows_by_n": rows,
+            "setup_s_with_autotune": t_setup,
+            "GBps": 112 * nodes * K / t_batch / 1e9,
+            "frac": 112 * nodes * K / t_batch / 1e9 / peak}
+
+
+def batch(args, pkg, torch):
+    print(json.dumps({"batch": True, **batch_measure(pkg, torch)}), flush=True)
+
+
+def variant(pkg, torch, flush, n, dim, mesh, prec, steps, Ra, peak):
+    """One single-cavity line beside the headline: MLUPS, algorithmic GB/s and
+    its fraction of the measured copy bandwidth, L2 flushed before every step."""
+    s = make_solver(pkg, n, mesh, Ra, prec, dim=dim)
+    t = timed_steps(pkg, s, steps, 3, flush, torch)
+    info = s.info
+    s.close()
+    nodes = n ** dim
+    b = 2 * (info.q_flow + info.q_temp) * BYTES_PER_VALUE[prec]
+    gbps = b * nodes / (t / steps) / 1e9
+    return {"MLUPS": nodes * steps / (t * 1e6), "GBps": gbps, "frac": gbps / peak,
+            "ms_per_step": 1e3 * t / steps, "steps": steps,
+            "kernel": KERNEL_NAMES.get(info.kernel, str(info.kernel))}
 
 
 def convergence(args, pkg, torch):
@@ -607,6 +713,140 @@ def validate3d(args, pkg, torch):
         s.close()
 
 
+# The paper's steady results (erf meshes, a = 1.5, Pr = 0.71): Table 2 and
+# Table 3 (2-D), the 3-D Nusselt / Reynolds table and the 3-D centre-value
+# table.  Keys: (dim, Ra) -> {N: values}, plus "inf" and "p" rows.
+PAPER_STEADY = {
+    (2, 1e6): {257: {"Nu": 8.8282, "Nu_hot": 8.8509, "Nu_middle": 8.8277, "Re": 99.6110},
+               513: {"Nu": 8.8202, "Nu_hot": 8.8317, "Nu_middle": 8.8200, "Re": 99.3839},
+               1025: {"Nu": 8.8188, "Nu_hot": 8.8246, "Nu_middle": 8.8188, "Re": 99.3576},
+               "inf": {"Nu": 8.8186, "Nu_hot": 8.8206, "Nu_middle": 8.8186, "Re": 99.3542},
+               "p": {"Nu": 2.6, "Nu_hot": 1.5, "Nu_middle": 2.6, "Re": 3.1}},
+    (2, 1e7): {513: {"Nu": 16.5245, "Nu_hot": 16.5461, "Nu_middle": 16.5243, "Re": 230.6601},
+               1025: {"Nu": 16.5133, "Nu_hot": 16.5242, "Nu_middle": 16.5133, "Re": 230.2448},
+               2049: {"Nu": 16.5114, "Nu_hot": 16.5169, "Nu_middle": 16.5114, "Re": 230.1948},
+               "inf": {"Nu": 16.5110, "Nu_hot": 16.5132, "Nu_middle": 16.5110, "Re": 230.1879},
+               "p": {"Nu": 2.5, "Nu_hot": 1.6, "Nu_middle": 2.6, "Re": 3.1}},
+    (2, 1e8): {513: {"Nu": 30.3130, "Nu_hot": 30.3503, "Nu_middle": 30.3125, "Re": 542.9352},
+               1025: {"Nu": 30.2225, "Nu_hot": 30.2423, "Nu_middle": 30.2223, "Re": 537.3420},
+               2049: {"Nu": 30.2072, "Nu_hot": 30.2172, "Nu_middle": 30.2072, "Re": 536.6449},
+               "inf": {"Nu": 30.2041, "Nu_hot": 30.2096, "Nu_middle": 30.2041, "Re": 536.5456},
+               "p": {"Nu": 2.6, "Nu_hot": 2.1, "Nu_middle": 2.6, "Re": 3.0}},
+    (3, 1e5): {129: {"Nu": 4.3406, "Nu_hot": 4.3624, "Nu_cold": 4.3624, "Re": 39.4521,
+                     "omega_c": 0.2565, "T_c": 0.49948, "u_c": -2.1342e-4, "v_c": 1.3056e-4},
+               181: {"Nu": 4.3363, "Nu_hot": 4.3520, "Nu_cold": 4.3520, "Re": 39.3768,
+                     "omega_c": 0.2560, "T_c": 0.49949, "u_c": -2.2689e-4, "v_c": 1.2423e-4},
+               257: {"Nu": 4.3346, "Nu_hot": 4.3457, "Nu_cold": 4.3457, "Re": 39.3500,
+                     "omega_c": 0.2557, "T_c": 0.49950, "u_c": -2.3377e-4, "v_c": 1.2119e-4},
+               "inf": {"Nu": 4.3334, "Nu_hot": 4.3362, "Nu_cold": 4.3362, "Re": 39.3352},
+               "p": {"Nu": 2.6, "Nu_hot": 1.5, "Nu_cold": 1.5, "Re": 3.0}},
+    (3, 1e6): {181: {"Nu": 8.6601, "Nu_hot": 8.6931, "Nu_cold": 8.6931, "Re": 97.4828,
+                     "omega_c": 0.1419, "T_c": 0.49942, "u_c": -1.2268e-4, "v_c": 1.4722e-5},
+               257: {"Nu": 8.6441, "Nu_hot": 8.6669, "Nu_cold": 8.6668, "Re": 97.0075,
+                     "omega_c": 0.1383, "T_c": 0.49946, "u_c": -1.3361e-4, "v_c": 1.6437e-5},
+               361: {"Nu": 8.6379, "Nu_hot": 8.6540, "Nu_cold": 8.6540, "Re": 96.8464,
+                     "omega_c": 0.1370, "T_c": 0.49948, "u_c": -1.3933e-4, "v_c": 1.7106e-5},
+               "inf": {"Nu": 8.6341, "Nu_hot": 8.6419, "Nu_cold": 8.6419, "Re": 96.7638},
+               "p": {"Nu": 2.8, "Nu_hot": 2.1, "Nu_cold": 2.1, "Re": 3.1}},
+    (3, 1e7): {181: {"Nu": 16.5341, "Nu_hot": 16.6161, "Nu_cold": 16.6158, "Re": 237.3925,
+                     "omega_c": 0.1296, "T_c": 0.49898, "u_c": -7.1568e-5, "v_c": 6.1396e-6},
+               257: {"Nu": 16.4179, "Nu_hot": 16.4681, "Nu_cold": 16.4680, "Re": 230.7625,
+                     "omega_c": 0.1149, "T_c": 0.49917, "u_c": -7.3572e-5, "v_c": 7.4064e-6},
+               361: {"Nu": 16.3670, "Nu_hot": 16.4001, "Nu_cold": 16.4001, "Re": 228.4148,
+                     "omega_c": 0.1094, "T_c": 0.49926, "u_c": -7.8387e-5, "v_c": 7.7847e-6},
+               "inf": {"Nu": 16.3274, "Nu_hot": 16.3422, "Nu_cold": 16.3422, "Re": 227.1278},
+               "p": {"Nu": 2.4, "Nu_hot": 2.3, "Nu_cold": 2.3, "Re": 3.0}},
+}
+
+
+def steady_run(pkg, torch, dim, n, Ra, init, tol, max_steps):
+    """One erf-mesh cavity (a = 1.5, FP32) from `init` (None: rest with the seeded
+    noise; else fields T, u, v[, w]) to a steady state: in 2-D the Nu-window
+    criterion (100 samples 1000 steps apart), in 3-D the field criterion of
+    Sec. 3 over 2000 steps.  Returns the reductions, centre values and fields."""
+    import numpy as np
+    from paper_2509_01099_gb300 import analysis as A
+    from synthetic import temperature_noise
+    xi = pkg.islbm_mesh_erf(n, 1.5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if dim == 2:
+        b = pkg.Batch([dict(n=n, mesh="erf", a=1.5, Ra=Ra)], precision="fp32")
+        s = b.members[0]
+    else:
+        b = None
+        s = pkg.Solver(xi, xi, xi, Ra=Ra, precision="fp32")
+    if init is None:
+        s.set_fields(temperature_noise(s.shape, 1e-6, seed=0))
+    else:
+        s.set_fields(init["T"], init["u"], init["v"], init.get("w"))
+    if dim == 2:
+        steps, _, _, st = b.run_to_steady_nu(tol=tol, sample=1000, window=100,
+                                             max_steps=max_steps, check=False)
+        steps = steps[0]
+    else:
+        r = s.run_to_steady(tol=tol, interval=2000, max_steps=max_steps, check=False)
+        steps, st = r["steps"], r["status"]
+    wall = time.perf_counter() - t0
+    red = s.reduce(check=False)
+    f = s.fields()
+    uf = s.info.u_f
+    fields = {k: np.asarray(v) for k, v in f.items()}
+    if dim == 2:
+        c = A.centre_values_2d(xi, xi, f["T"] + 0.5, f["u"] / uf, f["v"] / uf)
+    else:
+        c = A.centre_values_3d(xi, xi, xi, f["T"] + 0.5, f["u"] / uf, f["v"] / uf, f["w"] / uf)
+    out = {"n": n, "steps": int(steps), "status": int(st), "wall_s": wall,
+           "tf": steps / s.info.steps_per_tf, "kernel": s.info.kernel,
+           "Nu": red["Nu"], "Nu_hot": red["Nu_hot"], "Nu_cold": red["Nu_cold"],
+           "Nu_middle": red["Nu_middle"] if dim == 2 else None, "Re": red["Re"],
+           "Re_uv": red["Re_uv"], "T_c": c["T"], "u_c": c["u"], "v_c": c["v"],
+           "omega_c": abs(c["omega"])}
+    if b is not None:
+        b.close()
+    else:
+        s.close()
+    return out, {k: fields[k] for k in ("T", "u", "v") + (("w",) if dim == 3 else ())}
+
+
+def grid_study(args, pkg, torch):
+    """Steady cavities on a sequence of erf meshes (a = 1.5), coarse to fine,
+    each finer run started from the prolongated steady state of the one before
+    (grid sequencing: the transient is not repeated on the fine meshes); the
+    observed orders, Richardson-extrapolated values and GCI (Sec. 3) beside the
+    paper's rows for the same Ra."""
+    import math
+    from paper_2509_01099_gb300 import analysis as A
+    dim, Ra = args.dim, args.Ra
+    grids = [int(g) for g in args.grids.split(",")]
+    tol = 1e-6 if dim == 3 else (1e-5 if Ra >= 1e8 else 1e-6)
+    rows, prev, prev_n = [], None, None
+    for n in grids:
+        init = None
+        if prev is not None:
+            xc = pkg.islbm_mesh_erf(prev_n, 1.5)
+            xf = pkg.islbm_mesh_erf(n, 1.5)
+            init = A.prolong(prev, [xc] * dim, [xf] * dim)
+        row, fields = steady_run(pkg, torch, dim, n, Ra, init, tol,
+                                 args.max_steps or (12_000_000 if dim == 2 else 3_000_000))
+        row["started_from"] = prev_n
+        rows.append(row)
+        print(json.dumps({"grid_study_row": True, "dim": dim, "Ra": Ra, **row}), flush=True)
+        prev, prev_n = fields, n
+    table = None
+    if len(grids) == 3:
+        ratio = math.sqrt((grids[2] - 1) / (grids[0] - 1))
+        keys = ["Nu", "Nu_hot", "Re"] + (["Nu_middle"] if dim == 2 else ["Nu_cold"]) + \
+            ["T_c", "u_c", "v_c", "omega_c"]
+        table = A.convergence_table({k: tuple(r[k] for r in rows) for k in keys}, ratio=ratio)
+    print(json.dumps({"grid_study": True, "dim": dim, "Ra": Ra, "grids": grids,
+                      "criterion": ("Nu window means, 100 x 1000 steps, tol %g" % tol) if dim == 2
+                      else ("field change over 2000 steps below %g (Sec. 3)" % tol),
+                      "rows": rows, "richardson": table,
+                      "paper": {str(k): v for k, v in PAPER_STEADY.get((dim, Ra), {}).items()}}),
+          flush=True)
+
+
 def paper_scale(args, pkg, torch, flush):
     """The paper's own timing workloads (Sec. 3 and the 3-D performance
     paragraph): the 2-D cavity on an 8193^2 error-function mesh with a = 2.1 at
@@ -742,10 +982,13 @@ def main():
     if args.batch:
         batch(args, pkg, torch)
         return
+    if args.grid_study:
+        grid_study(args, pkg, torch)
+        return
     solver = make_solver(pkg, n, args.mesh, args.Ra, args.precision, args.kernel, dim)
     info = solver.info
 
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(gpu_selector(local))
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
@@ -763,6 +1006,10 @@ def main():
     peak, peak_src = (pk["hbm_gbs"], "measured") if pk else (6800.0, "fallback")
 
     # ---- end to end through the C ABI with host buffers ----
+    # One iteration: the initial fields from pinned host memory (equilibrium
+    # initialisation), `inner` time steps, the reductions and the fields T, u,
+    # v (, w) back to host memory.  Reported per time step: the copies of an
+    # iteration divided by its `inner` steps.
     inner = 100
     pin = lambda: torch.empty(nodes, dtype=torch.float64, pin_memory=True).numpy()
     hT, hu, hv = pin(), pin(), pin()
@@ -773,31 +1020,40 @@ def main():
     if hw is not None:
         hw[:] = 0.0
     e2e_iters = max(3, min(20, args.steps // inner))
+    hout = {k: pin() for k in ("rho", "T", "u", "v") + (("w",) if dim == 3 else ())}
     solver.set_fields(hT, hu, hv, hw)
     solver.step(inner)
     solver.reduce(check=False)
+    solver.fields(out=hout)
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_iters):
-        solver.set_fields(hT, hu, hv, hw)    # H2D of the step's inputs (pinned)
+        solver.set_fields(hT, hu, hv, hw)    # H2D of the inputs (pinned)
         solver.step(inner)
-        solver.reduce(check=False)           # D2H of the result (Nu, Re, mass, ...)
+        solver.reduce(check=False)           # D2H of the reductions (Nu, Re, mass, ...)
+        out = solver.fields(out=hout)        # D2H of the fields rho, T, u, v (, w), pinned
     t_e2e = max_over_ranks(world, time.perf_counter() - t0)
     e2e_value = world * nodes * inner * e2e_iters / (t_e2e * 1e6)
+    h2d = (dim + 1) * 8 * nodes
+    d2h = 8 * 16 + sum(a.nbytes for a in out.values())
 
     variants = {}
-    if not args.no_variants and dim == 2:
+    if not args.no_variants and dim == 2 and rank == 0:
+        k = min(args.steps, 500)
         for mesh, prec in (("uniform", "fp32"), ("tanh", "fp16dev"), ("uniform", "fp16dev"),
                            ("tanh", "bf16dev")):
-            s2 = make_solver(pkg, n, mesh, args.Ra, prec)
-            t2 = timed_steps(pkg, s2, min(args.steps, 500), 10, flush, torch)
-            k = min(args.steps, 500)
-            b2 = 2 * 14 * BYTES_PER_VALUE[prec]
-            variants[f"{mesh}_{prec}"] = {
-                "MLUPS": nodes * k / (t2 * 1e6),
-                "GBps": b2 * nodes / (t2 / k) / 1e9,
-                "ms_per_step": 1e3 * t2 / k}
-            s2.close()
+            variants[f"{mesh}_{prec}"] = variant(pkg, torch, flush, n, 2, mesh, prec, k, args.Ra,
+                                                 peak)
+        # far above L2: the roofline regime (4096^2, 2 x 1.9 GB of FP32 state)
+        for prec in ("fp32", "bf16dev"):
+            variants[f"tanh4096_{prec}"] = variant(pkg, torch, flush, 4096, 2, "tanh", prec,
+                                                   min(args.steps, 50), args.Ra, peak)
+        # the 3-D cavity workload: 256^3 tanh mesh, Ra = 1e7
+        for prec in ("fp32", "bf16dev"):
+            variants[f"cube256_tanh_{prec}"] = variant(pkg, torch, flush, 256, 3, "tanh", prec,
+                                                       min(args.steps, 20), 1e7, peak)
+        # the 64-cavity batched sweep against the same cavities stepped one by one
+        variants["batch64_fp32"] = batch_measure(pkg, torch, K=64, warm=64)
 
     if rank == 0:
         line = {
@@ -811,6 +1067,13 @@ def main():
                        "n": n, "mesh": args.mesh, "a": 1.5, "Ra": args.Ra, "Pr": 0.71,
                        "precision": args.precision, "parallelism": f"replicas{world}",
                        "l2": "before every timed step: 256 MB write, then 256 MB read of another buffer (cold, clean L2)",
+                       "l2_regime": (f"state {bytes_per_update * nodes / 1e6:.0f} MB "
+                                     f"(two time levels) against a 126 MB L2: "
+                                     + ("reads come from DRAM, but much of what a step writes "
+                                        "is still in L2 when it ends; frac is algorithmic bytes "
+                                        "over time, the DRAM traffic is in roofline.traffic"
+                                        if bytes_per_update * nodes < 2.5e8 else
+                                        "far above L2, every step streams from and to DRAM")),
                        "L_lu": info.L, "steps_per_tf": info.steps_per_tf},
             "wctpdt_s": ms_per_step * 1e-3 * info.steps_per_tf,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -819,15 +1082,18 @@ def main():
                          "bytes_per_update": bytes_per_update,
                          "kernel": KERNEL_NAMES.get(info.kernel, str(info.kernel))},
             "e2e": {"value": e2e_value, "unit": "MLUPS",
-                    "h2d_bytes_per_step": (dim + 1) * 8 * nodes, "d2h_bytes_per_step": 8 * 16,
-                    "definition": f"per step: set_fields from pinned host T,u,v + {inner} time steps + reduce read back"},
+                    "h2d_bytes_per_step": h2d / inner, "d2h_bytes_per_step": d2h / inner,
+                    "definition": (f"iterations of: set_fields from pinned host T, u, v "
+                                   f"({h2d} B), {inner} time steps, the reductions and "
+                                   f"get_fields of rho, T, u, v back to the host ({d2h} B); "
+                                   f"bytes per time step = per iteration / {inner}")},
             "gpu_launches": args.steps,
             "clocks": clk,
             "state_check": {"Nu": red.get("Nu"), "Re": red.get("Re"), "status": red.get("status")},
             "variants": variants,
         }
         if not args.no_cpu_baseline and dim == 2:
-            line["cpu_baseline"] = cpu_baseline(n, 6, args.mesh)
+            line["cpu_baseline"] = cpu_baseline(n, 4, args.mesh)
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

@@ -162,13 +162,43 @@ def centre_values_2d(xi_x, xi_y, T, u, v):
 
 
 def centre_values_3d(xi_x, xi_y, xi_z, T, u, v, w):
-    """T, u, v, w at the centre of the cube (the 3-D centre-value table; fields
-    [nz][ny][nx])."""
-    px = _centre_pair(node_positions(xi_x))
-    py = _centre_pair(node_positions(xi_y))
-    pz = _centre_pair(node_positions(xi_z))
+    """T, u, v, w and the magnitude of the vorticity vector (dw/dy - dv/dz,
+    du/dz - dw/dx, dv/dx - du/dy) at the centre of the cube (the 3-D
+    centre-value table; fields [nz][ny][nx], derivatives per unit x*)."""
+    x, y, z = node_positions(xi_x), node_positions(xi_y), node_positions(xi_z)
+    px, py, pz = _centre_pair(x), _centre_pair(y), _centre_pair(z)
     c = [(2, px), (1, py), (0, pz)]
-    return {k: _at_centre(f, c) for k, f in (("T", T), ("u", u), ("v", v), ("w", w))}
+    out = {k: _at_centre(f, c) for k, f in (("T", T), ("u", u), ("v", v), ("w", w))}
+
+    def d(f, coord, axis):
+        others = [(a, p) for a, p in ((2, px), (1, py), (0, pz)) if a != axis]
+        return _centre_derivative(f, coord, axis, others)
+
+    wx = d(w, y, 1) - d(v, z, 0)
+    wy = d(u, z, 0) - d(w, x, 2)
+    wz = d(v, x, 2) - d(u, y, 1)
+    out["omega"] = float(np.sqrt(wx * wx + wy * wy + wz * wz))
+    out["omega_z"] = wz
+    return out
+
+
+def prolong(fields, coarse, fine):
+    """Fields of a coarse mesh carried to a finer one by multilinear
+    interpolation between node positions (linear extrapolation into the
+    layer between the outermost coarse nodes and the walls): the initial
+    state of a finer run in a grid-refinement study.  `coarse` and `fine` are
+    lists of ghost-node meshes per axis (x first); fields are arrays
+    [(nz,) ny, nx]."""
+    from scipy.interpolate import RegularGridInterpolator
+    pc = [node_positions(m) for m in reversed(coarse)]      # array axis order
+    pf = [node_positions(m) for m in reversed(fine)]
+    pts = np.stack(np.meshgrid(*pf, indexing="ij"), axis=-1).reshape(-1, len(pf))
+    out = {}
+    for k, f in fields.items():
+        it = RegularGridInterpolator(pc, np.asarray(f, dtype=np.float64), method="linear",
+                                     bounds_error=False, fill_value=None)
+        out[k] = it(pts).reshape([len(a) for a in pf])
+    return out
 
 
 def band_profiles_3d(field, y_star, z_star, band=(0.4, 0.6), wy=None, wz=None):

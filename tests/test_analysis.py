@@ -142,3 +142,39 @@ def test_divergence_3d_and_its_pdf():
     assert abs(pdf["median_log10"] + 5) < 0.02
     zero = A.divergence_pdf(np.zeros(10))
     assert zero["below"] == 1.0
+
+
+def test_centre_vorticity_3d_of_rigid_rotations():
+    import numpy as np
+    xi_x, xi_y, xi_z = _mesh_xy("erf", 9), _mesh_xy("uniform", 10), _mesh_xy("erf", 11)
+    x, y, z = (A.node_positions(m) for m in (xi_x, xi_y, xi_z))
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    T = 0 * X
+    # rotation about z: (u, v, w) = (-(y-1/2), x-1/2, 0): vorticity (0, 0, 2)
+    c = A.centre_values_3d(xi_x, xi_y, xi_z, T, -(Y - 0.5), X - 0.5, 0 * X)
+    assert abs(c["omega"] - 2) < 1e-12 and abs(c["omega_z"] - 2) < 1e-12
+    # rotation about x with rate 3: (0, -3(z-1/2), 3(y-1/2)): vorticity (6, 0, 0)
+    c = A.centre_values_3d(xi_x, xi_y, xi_z, T, 0 * X, -3 * (Z - 0.5), 3 * (Y - 0.5))
+    assert abs(c["omega"] - 6) < 1e-12 and abs(c["omega_z"]) < 1e-12
+
+
+def test_prolong_is_exact_on_linear_fields():
+    import numpy as np
+    from oracle import islbm_oracle as O
+    coarse = [O.mesh_erf(9, 1.5), O.mesh_erf(7, 1.5)]
+    fine = [O.mesh_erf(17, 1.5), O.mesh_erf(13, 1.5)]
+    xc, yc = A.node_positions(coarse[0]), A.node_positions(coarse[1])
+    xf, yf = A.node_positions(fine[0]), A.node_positions(fine[1])
+    Yc, Xc = np.meshgrid(yc, xc, indexing="ij")
+    Yf, Xf = np.meshgrid(yf, xf, indexing="ij")
+    out = A.prolong({"T": 0.3 + 2 * Xc - Yc}, coarse, fine)
+    np.testing.assert_allclose(out["T"], 0.3 + 2 * Xf - Yf, atol=1e-13)
+    # 3-D, with extrapolation into the wall layers
+    c3 = [O.mesh_erf(5, 1.5)] * 3
+    f3 = [O.mesh_erf(9, 1.5)] * 3
+    p = A.node_positions(c3[0])
+    q = A.node_positions(f3[0])
+    Z, Y, X = np.meshgrid(p, p, p, indexing="ij")
+    Zf, Yf, Xf = np.meshgrid(q, q, q, indexing="ij")
+    out = A.prolong({"u": X + 2 * Y + 3 * Z}, c3, f3)
+    np.testing.assert_allclose(out["u"], Xf + 2 * Yf + 3 * Zf, atol=1e-12)
