@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ISLBM MLUPS & %HBM roofline; wall time to steady Nu, plain vs mixed/learned"
 WORKLOAD = "2-D side-heated cavity, D2Q9+D2Q5, Ra=1e8, Pr=0.71, 1024x1024 tanh-stretched mesh (a=1.5)"
-BYTES_PER_VALUE = {"fp64": 8, "fp32": 4, "fp16dev": 2, "bf16dev": 2}
+BYTES_PER_VALUE = {"fp64": 8, "fp32": 4, "fp16dev": 2, "bf16dev": 2, "fp16neq": 2}
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16dev": "f16", "bf16dev": "bf16"}
 
 
@@ -70,6 +70,9 @@ def parse():
                     help="3-D cavity to steady state against the paper's 3-D table (129^3, Ra=1e5)")
     ap.add_argument("--batch-steady", action="store_true",
                     help="the 64-cavity sweep to a steady Nu: batch vs a costed sequential loop")
+    ap.add_argument("--timed-sequential", action="store_true",
+                    help="with --batch-steady: also run the 64 cavities one after the other to "
+                         "a steady Nu and time that loop")
     ap.add_argument("--series", action="store_true",
                     help="1024^2 Ra=1e8 for --series-steps steps with Nu every 1000 steps")
     ap.add_argument("--series-steps", type=int, default=200_000)
@@ -398,16 +401,17 @@ WARMSTART_WEIGHTS = os.path.join(ROOT, "paper_2509_01099_gb300", "weights", "war
 def steady(args, pkg, torch):
     """Wall time to a steady Nu on the 256^2 tanh-stretched cavity (a = 1.5) for
     16 held-out Ra log-uniform in [1e6, 1e8] (PCG64 seed 2): plain (FP32 from
-    rest), mixed (FP16 / BF16 deviation storage from rest) and learned (FP32 and
-    FP16 started from the warm-start network's prediction).  Each arm is one
+    rest), mixed (FP16 / BF16 deviation storage and FP16 non-equilibrium storage
+    from rest) and learned (FP32, FP16 deviations and FP16 non-equilibrium
+    storage started from the warm-start network's prediction).  Each arm is one
     batch of the 16 cavities run until every window mean of Nu (100 samples
     1000 steps apart) changes by at most 2e-4 (islbm_batch_run_to_steady_nu)."""
     from paper_2509_01099_gb300 import warmstart as ws
     from synthetic import ra_sweep
     ras = ra_sweep(16, seed=2)[0]
     net = ws.load(WARMSTART_WEIGHTS)
-    arms = (("fp32", "rest"), ("fp16dev", "rest"), ("bf16dev", "rest"), ("fp32", "warm"),
-            ("fp16dev", "warm"))
+    arms = (("fp32", "rest"), ("fp16dev", "rest"), ("bf16dev", "rest"), ("fp16neq", "rest"),
+            ("fp32", "warm"), ("fp16dev", "warm"), ("fp16neq", "warm"))
     res = ws.compare(net, ras, arms=arms)
     plain = res["fp32/rest"]
     summary = {}
@@ -422,6 +426,34 @@ def steady(args, pkg, torch):
                       "in [1e6, 1e8] (seed 2)", "criterion": "Nu window means, 100 x 1000 steps, "
                       "tol 2e-4", "Ra": [float(r) for r in ras], "summary": summary,
                       "arms": res}), flush=True)
+
+
+def steady_lines(pkg, count=4, max_steps=2_000_000):
+    """The second half of the metric on a bounded sample: `count` of the 16
+    held-out Ra (PCG64 seed 2) of the 256^2 tanh cavity (a = 1.5), each arm one
+    batch run to the steady-Nu criterion (window means of 100 samples 1000
+    steps apart agreeing to 2e-4): plain FP32 from rest, the learned warm start
+    (FP32, including the network's inference), BF16-deviation storage and FP16
+    non-equilibrium storage from rest (step budgets capped at `max_steps`).
+    Wall times and the largest Nu / Re deviation from the plain arm."""
+    from paper_2509_01099_gb300 import warmstart as ws
+    from synthetic import ra_sweep
+    ras = ra_sweep(16, seed=2)[0][:count]
+    net = ws.load(WARMSTART_WEIGHTS)
+    res = ws.compare(net, ras, arms=(("fp32", "rest"), ("fp32", "warm"), ("bf16dev", "rest"),
+                                     ("fp16neq", "rest")),
+                     max_steps=max_steps)
+    plain = res["fp32/rest"]
+    out = {"Ra": [float(r) for r in ras]}
+    for key, name in (("fp32/rest", "plain"), ("fp32/warm", "learned"),
+                      ("bf16dev/rest", "mixed_bf16"), ("fp16neq/rest", "mixed_fp16neq")):
+        arm = res[key]
+        out[name] = {"wall_s": arm["wall_s"], "steps_total": int(sum(arm["steps"])),
+                     "all_steady": arm["status"] == 0,
+                     "wall_rel_to_plain": arm["wall_s"] / plain["wall_s"],
+                     "max_Nu_dev": max(abs(a / b - 1) for a, b in zip(arm["Nu"], plain["Nu"])),
+                     "max_Re_dev": max(abs(a / b - 1) for a, b in zip(arm["Re"], plain["Re"]))}
+    return out
 
 
 def batch_measure(pkg, torch, K=640, warm=128):
@@ -493,7 +525,7 @@ def variant(pkg, torch, flush, n, dim, mesh, prec, steps, Ra, peak):
     info = s.info
     s.close()
     nodes = n ** dim
-    b = 2 * (info.q_flow + info.q_temp) * BYTES_PER_VALUE[prec]
+    b = info.bytes_per_update      # read + write of one node's state (FP16NEQ: 2 x 44 B)
     gbps = b * nodes / (t / steps) / 1e9
     return {"MLUPS": nodes * steps / (t * 1e6), "GBps": gbps, "frac": gbps / peak,
             "ms_per_step": 1e3 * t / steps, "steps": steps,
@@ -606,9 +638,31 @@ def batch_steady(args, pkg, torch):
     done = [k for k in steps if k > 0]
     seq = sum(per_step[int(n)] * (k if k > 0 else (args.max_steps or 4_000_000))
               for n, k in zip(ns, steps))
+    timed = None
+    if args.timed_sequential:
+        # the same cavities, one at a time, each from the same initial state to
+        # the same criterion (a batch of one member: the same kernel and the
+        # same steady test)
+        seq_steps, seq_nu = [], []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k, c in enumerate(cavs):
+            b1 = pkg.Batch([c], precision="fp32", autotune=True)
+            m1 = b1.members[0]
+            m1.set_fields(temperature_noise(m1.shape, 1e-6, seed=k))
+            s1, nu1, _, _ = b1.run_to_steady_nu(tol=2e-4, sample=1000, window=100,
+                                                max_steps=args.max_steps or 4_000_000,
+                                                check=False)
+            seq_steps.append(s1[0])
+            seq_nu.append(nu1[0])
+            b1.close()
+        timed = {"wall_s": time.perf_counter() - t0, "steps": seq_steps, "Nu": seq_nu,
+                 "same_steps_as_batch": seq_steps == list(steps)}
     print(json.dumps({"batch_steady": True, "cavities": len(cavs), "status": int(st),
                       "converged": len(done), "wall_s_batch": wall,
                       "wall_s_sequential_costed": seq, "speedup": seq / wall,
+                      "sequential_timed": timed,
+                      "speedup_timed": (timed["wall_s"] / wall) if timed else None,
                       "steps": steps, "Ra": [float(r) for r in ra], "n": [int(n) for n in ns],
                       "Nu": nu, "Re": re, "single_cavity_s_per_step": per_step}), flush=True)
 
@@ -1000,7 +1054,7 @@ def main():
 
     ms_per_step = 1e3 * t_dev / args.steps
     value = world * nodes * args.steps / (t_dev * 1e6)
-    bytes_per_update = 2 * (info.q_flow + info.q_temp) * BYTES_PER_VALUE[args.precision]
+    bytes_per_update = info.bytes_per_update
     achieved = bytes_per_update * nodes / (t_dev / args.steps) / 1e9
     pk = peaks()
     peak, peak_src = (pk["hbm_gbs"], "measured") if pk else (6800.0, "fallback")
@@ -1041,11 +1095,11 @@ def main():
     if not args.no_variants and dim == 2 and rank == 0:
         k = min(args.steps, 500)
         for mesh, prec in (("uniform", "fp32"), ("tanh", "fp16dev"), ("uniform", "fp16dev"),
-                           ("tanh", "bf16dev")):
+                           ("tanh", "bf16dev"), ("tanh", "fp16neq")):
             variants[f"{mesh}_{prec}"] = variant(pkg, torch, flush, n, 2, mesh, prec, k, args.Ra,
                                                  peak)
         # far above L2: the roofline regime (4096^2, 2 x 1.9 GB of FP32 state)
-        for prec in ("fp32", "bf16dev"):
+        for prec in ("fp32", "bf16dev", "fp16neq"):
             variants[f"tanh4096_{prec}"] = variant(pkg, torch, flush, 4096, 2, "tanh", prec,
                                                    min(args.steps, 50), args.Ra, peak)
         # the 3-D cavity workload: 256^3 tanh mesh, Ra = 1e7
@@ -1054,6 +1108,8 @@ def main():
                                                        min(args.steps, 20), 1e7, peak)
         # the 64-cavity batched sweep against the same cavities stepped one by one
         variants["batch64_fp32"] = batch_measure(pkg, torch, K=64, warm=64)
+        # wall time to a steady Nu: plain, learned warm start, mixed precision
+        variants["steady_256_4ra"] = steady_lines(pkg)
 
     if rank == 0:
         line = {

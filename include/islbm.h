@@ -64,12 +64,19 @@ typedef enum { ISLBM_D2Q9_D2Q5 = 0, ISLBM_D3Q19_D3Q7 = 1 } islbm_lattice;
 /* Storage type of the populations.  Collision and interpolation run in FP64
  * for ISLBM_FP64 and in FP32 otherwise.  All forms store the deviation from
  * the rest state, f_i - w_i (flow) and g_i (temperature, T0 = 0); FP16DEV and
- * BF16DEV store those deviations in 16 bits. */
+ * BF16DEV store those deviations in 16 bits (stochastically rounded).
+ * ISLBM_FP16NEQ (2-D only, the centred stencil, kernel variants 4 and 5 of
+ * islbm_params.kernel; ISLBM_ERR_ARG otherwise, and for the slab calls) splits each node's deviations into its moments (drho, jx, jy, T) in
+ * FP32 and, per population, the remainder beyond the equilibrium of those
+ * moments in FP16 (scaled by 2^12, rounded to nearest): 44 bytes a node
+ * against 56 (FP32) and 28 (FP16DEV), with the remainder, which carries the
+ * stress and heat flux, resolved to about 1e-8 instead of 1e-5. */
 typedef enum {
   ISLBM_FP64 = 0,
   ISLBM_FP32 = 1,
   ISLBM_FP16DEV = 2,
-  ISLBM_BF16DEV = 3
+  ISLBM_BF16DEV = 3,
+  ISLBM_FP16NEQ = 4
 } islbm_precision;
 
 /* Interpolation stencil of the virtual streaming (Sec. 2.2): three nodes
@@ -300,15 +307,16 @@ typedef struct islbm_batch* islbm_batch_t;
  * return the fastest in *best; us_per_step (host, may be NULL) receives
  * ISLBM_KERNEL_VARIANTS entries (+inf for variants that cannot run).  Results
  * are cached per (n, mesh, a, precision) for the life of the process.
- * FP32 / FP16DEV / BF16DEV only. */
+ * FP32 / FP16DEV / BF16DEV / FP16NEQ (which runs variants 4 and 5 only). */
 #define ISLBM_KERNEL_VARIANTS 10
 ISLBM_API islbm_status islbm_autotune(int n, int mesh, double a, int precision, void* stream,
                                       int* best, double* us_per_step);
 
 /* Create a batch of `count` cavities (host array, copied) with one storage
- * precision (FP32 / FP16DEV / BF16DEV).  opt: common parameters (NULL =
- * defaults).  autotune != 0 chooses each mesh size's tile height with
- * islbm_autotune; otherwise 8-row tiles.  stream: shared by all members. */
+ * precision (FP32 / FP16DEV / BF16DEV / FP16NEQ).  opt: common parameters
+ * (NULL = defaults).  autotune != 0 chooses each mesh size's tile height with
+ * islbm_autotune (FP16NEQ: always 8 rows); otherwise 8-row tiles.  stream:
+ * shared by all members. */
 ISLBM_API islbm_status islbm_batch_create(int count, const islbm_cavity* cavities, int precision,
                                           const islbm_params* opt, int autotune, void* stream,
                                           islbm_batch_t* out);
@@ -359,18 +367,36 @@ ISLBM_API islbm_status islbm_batch_run_to_steady_nu(islbm_batch_t b, double tol,
  * `stream`, returns ISLBM_ERR_ARG for NULL pointers or bad sizes (nothing
  * launched) and ISLBM_ERR_CUDA if the launch fails.  Tensors are NHWC, FP32
  * unless stated; "bf16" buffers hold __nv_bfloat16. */
-/* C[M,N] (+)= op(A) op(B) (+ bias[N]) on the tensor cores (mma.sync BF16, FP32
- * accumulation).  transA = 0: A is M x K row-major with leading dimension lda;
- * 1: A is K x M row-major.  transB = 0: B is K x N row-major; 1: N x K.
+/* C[M,N] (+)= op(A) op(B) (+ bias[N]) on the tensor cores, BF16 operands with
+ * FP32 accumulation.  transA = 0: A is M x K row-major with leading dimension
+ * lda; 1: A is K x M row-major.  transB = 0: B is K x N row-major; 1: N x K.
  * accumulate != 0 adds to C.  A, B: bf16; C, bias: FP32 (bias may be NULL).
- * When the output tiles are too few to fill the GPU the K range is split
- * over blocks that add their parts with FP32 atomics (summation order then
- * varies from run to run).  ISLBM_ERR_ARG also for ldc < N or a leading
- * dimension of A or B shorter than its row. */
+ * Path: when lda and ldb are multiples of 8 and A, B are 16-byte aligned, the
+ * fifth-generation tensor cores (tcgen05.mma, accumulator in tensor memory;
+ * 128 x N tiles, 64-wide k stages); else the warp-level mma.sync kernel.
+ * When the output tiles are too few to fill the GPU the K range is split and
+ * the splits' partial tiles are added in a fixed order, so results do not
+ * depend on scheduling.  The partial tiles live in one split-K workspace per
+ * device, allocated through the registered allocator and grown on demand
+ * (the device is synchronised while it grows): calls that split K, and
+ * islbm_cnn_colsum, must not run concurrently on different streams of one
+ * device.  ISLBM_ERR_ARG also for ldc < N or a leading dimension of A or B
+ * shorter than its row; ISLBM_ERR_OOM when the workspace cannot grow. */
 ISLBM_API islbm_status islbm_cnn_gemm_bf16(const void* A, const void* B, float* C,
                                            const float* bias, int M, int N, int K, int lda,
                                            int ldb, int ldc, int transA, int transB,
                                            int accumulate, void* stream);
+/* The same product with the path chosen: 0 as islbm_cnn_gemm_bf16, 1 the
+ * mma.sync kernel, 2 the tcgen05 kernel (ISLBM_ERR_ARG when its conditions
+ * above do not hold). */
+ISLBM_API islbm_status islbm_cnn_gemm_bf16_ex(const void* A, const void* B, float* C,
+                                              const float* bias, int M, int N, int K, int lda,
+                                              int ldb, int ldc, int transA, int transB,
+                                              int accumulate, int path, void* stream);
+/* *timed_out = 1 if a bounded mbarrier wait of the tcgen05 GEMM gave up since
+ * the last reset (its output tile is then not written); reset != 0 clears the
+ * flag.  Reads device memory (synchronous). */
+ISLBM_API islbm_status islbm_cnn_check_timeout(int reset, int* timed_out);
 /* 3x3 zero-padded im2col of in[B,H,W,C] into bf16 rows col[B*H*W][kpad]
  * ordered [dy][dx][c]; kpad >= 9C, the extra columns are zero. */
 ISLBM_API islbm_status islbm_cnn_im2col(const float* in, void* col, int B, int H, int W, int C,
@@ -387,8 +413,9 @@ ISLBM_API islbm_status islbm_cnn_tanh(float* x, long long n, void* stream);
 ISLBM_API islbm_status islbm_cnn_tanh_back(const float* y, float* dy, long long n, void* stream);
 /* FP32 -> bf16 copy of n values. */
 ISLBM_API islbm_status islbm_cnn_to_bf16(const float* x, void* y, long long n, void* stream);
-/* out[N] (+)= column sums of the M x N row-major x (chunks of rows are added
- * with FP32 atomics; the order varies). */
+/* out[N] (+)= column sums of the M x N row-major x.  Chunks of 2048 rows are
+ * summed in the split-K workspace and added in a fixed order (deterministic);
+ * ISLBM_ERR_OOM when the workspace cannot grow. */
 ISLBM_API islbm_status islbm_cnn_colsum(const float* x, float* out, int M, int N, int accumulate,
                                         void* stream);
 /* Weighted mean squared error of y against t (n values, channel weights wc of
@@ -430,6 +457,24 @@ ISLBM_API islbm_status islbm_debug_bounds(int reset, int* flagged);
  * ISLBM_OK if the wait somehow completed, ISLBM_ERR_CUDA / ISLBM_ERR_OOM on a
  * CUDA failure.  Synchronises `stream`; the context stays usable. */
 ISLBM_API islbm_status islbm_selftest_wait_timeout(void* stream);
+
+/* ---- device memory --------------------------------------------------------------
+ * Every device allocation of the library (a handle's population buffers,
+ * tables, scratch and staging buffers, a batch's work lists, the network
+ * GEMM's split-K workspace) goes through the allocator registered here, or,
+ * when none is, cudaMallocAsync / cudaFreeAsync on the owner's stream (the
+ * handle's or the batch's; the legacy stream for the workspace).  alloc
+ * returns a device pointer of at least `bytes` bytes on device `device` for
+ * use on `stream` (NULL on failure, which the calling entry point reports as
+ * ISLBM_ERR_OOM); release returns one.  A handle keeps the allocator it was
+ * created with: registering another later does not change how its memory is
+ * freed.  Both functions or neither (NULL, NULL restores the default);
+ * ISLBM_ERR_ARG otherwise.  Not a method of the paper: memory plumbing.  The
+ * Python binding registers torch's caching allocator when torch has CUDA. */
+typedef void* (*islbm_alloc_fn)(size_t bytes, int device, void* stream, void* ctx);
+typedef void (*islbm_free_fn)(void* ptr, int device, void* stream, void* ctx);
+ISLBM_API islbm_status islbm_set_allocator(islbm_alloc_fn alloc, islbm_free_fn release,
+                                           void* ctx);
 
 /* ---- 2-D slab decomposition ---------------------------------------------------
  * The time step of Sec. 2.2 needs, at a node, the post-collision populations

@@ -14,6 +14,6 @@ from .islbm import (EXPORTS, KERNEL_VARIANTS, KERNELS, LATTICES, MESH_KINDS, PRE
                     islbm_steady_change, islbm_step, islbm_synchronize, library_path,
                     load_library, islbm_set_row_range, islbm_get_rows, islbm_set_rows,
                     islbm_reduce_sums, islbm_finish_sums, rows_bytes, REDUCTION_SUMS,
-                    SUM_MAX_SLOT)
+                    SUM_MAX_SLOT, islbm_set_allocator, torch_allocator)
 
 __all__ = [n for n in dir() if not n.startswith("_")]

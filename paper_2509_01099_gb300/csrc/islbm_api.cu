@@ -136,10 +136,12 @@ std::string encode_tensor_maps(Solver* s) {
     return "cuTensorMapEncodeTiled is not available";
   const int R = (s->variant == KV_TMA_R2S2 || s->variant == KV_TMA_R2S3) ? 2 : 4;
   const int hx = 16 / (int)s->elem;
-  const CUtensorMapDataType dt = s->precision == ISLBM_FP32
-                                     ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                     : (s->precision == ISLBM_FP16DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  const CUtensorMapDataType dt =
+      s->precision == ISLBM_FP32
+          ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+          : (s->precision == ISLBM_FP16DEV || s->precision == ISLBM_FP16NEQ
+                 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
   if (s->dim == 3 && is_zm3d(s->variant)) {
     // z-marching kernels: one descriptor per staging group.  Its base is the
     // group's first plane; the dimensions are (x over the padded pitch, y, z,
@@ -202,11 +204,72 @@ std::string encode_tensor_maps(Solver* s) {
         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    // FP16NEQ: the 4 FP32 moment planes after the 14 remainder planes, a box
+    // of the tile with one 16-byte chunk (4 columns) of halo on each side
+    const cuuint64_t mdims[3] = {(cuuint64_t)s->pitch, (cuuint64_t)s->n[1], 4};
+    const cuuint64_t mstrides[2] = {(cuuint64_t)s->pitch * 4, (cuuint64_t)s->plane * 4};
+    const cuuint32_t mbox[3] = {64 + 8, (cuuint32_t)(4 * R + 2), 4};
+    void* mbase = static_cast<char*>(s->buf[b]) + (size_t)14 * s->plane * s->elem;
+    if (s->precision == ISLBM_FP16NEQ) {
+      r = reinterpret_cast<EncodeFn>(fn)(
+          reinterpret_cast<CUtensorMap*>(s->tmap_m[b]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, mbase,
+          mdims, mstrides, mbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    } else {
+      std::memcpy(s->tmap_m[b], s->tmap[b], sizeof(s->tmap_m[b]));
+    }
   }
   return "";
 }
 
 }  // namespace
+
+namespace {
+std::mutex g_alloc_mutex;
+islbm::DevAllocator g_alloc;
+}  // namespace
+
+islbm::DevAllocator islbm::current_allocator() {
+  std::lock_guard<std::mutex> lock(g_alloc_mutex);
+  return g_alloc;
+}
+
+cudaError_t islbm::dev_alloc(const DevAllocator& a, void** p, size_t bytes,
+                             cudaStream_t stream) {
+  *p = nullptr;
+  if (a.alloc) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    *p = a.alloc(bytes, dev, stream, a.ctx);
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(p, bytes, stream);
+}
+
+void islbm::dev_free(const DevAllocator& a, void* p, cudaStream_t stream) {
+  if (!p) return;
+  if (a.alloc) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (a.release) a.release(p, dev, stream, a.ctx);
+    return;
+  }
+  cudaFreeAsync(p, stream);
+}
+
+extern "C" islbm_status islbm_set_allocator(islbm_alloc_fn alloc, islbm_free_fn release,
+                                            void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr))
+    return fail(nullptr, ISLBM_ERR_ARG, "islbm_set_allocator: give both functions or neither");
+  std::lock_guard<std::mutex> lock(g_alloc_mutex);
+  g_alloc.alloc = alloc;
+  g_alloc.release = release;
+  g_alloc.ctx = ctx;
+  return ISLBM_OK;
+}
 
 cudaError_t islbm::launch_setup_once(const void* kernel,
                                      cudaError_t (*setup)(const void*, int*), int* value) {
@@ -347,7 +410,7 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
   *out = nullptr;
   if (lattice != ISLBM_D2Q9_D2Q5 && lattice != ISLBM_D3Q19_D3Q7)
     return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: unknown lattice");
-  if (precision < ISLBM_FP64 || precision > ISLBM_BF16DEV)
+  if (precision < ISLBM_FP64 || precision > ISLBM_FP16NEQ)
     return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: unknown precision");
   const int dim = lattice == ISLBM_D2Q9_D2Q5 ? 2 : 3;
   if ((dim == 2) != (xi_z == nullptr))
@@ -363,6 +426,12 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
   if (prm.kernel < 0 || prm.kernel >= KV_COUNT ||
       (dim == 2 && (prm.kernel == KV_TMA_3D || is_zm3d(prm.kernel))))
     return fail(nullptr, ISLBM_ERR_ARG, "islbm_create: unknown kernel variant");
+  if (precision == ISLBM_FP16NEQ &&
+      (dim != 2 || prm.stencil != ISLBM_STENCIL_CENTRED ||
+       (prm.kernel != KV_AUTO && prm.kernel != KV_TMA_R2S2 && prm.kernel != KV_TMA_R2S3)))
+    return fail(nullptr, ISLBM_ERR_ARG,
+                "islbm_create: FP16NEQ storage needs the 2-D lattice, the centred stencil and "
+                "kernel variant 0, 4 or 5");
   const double* xis[3] = {xi_x, xi_y, xi_z};
   const int ns[3] = {nx, ny, dim == 3 ? nz : 1};
   const char* names[3] = {"xi_x", "xi_y", "xi_z"};
@@ -472,6 +541,8 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
   // (and the 3-D pipelined kernel for stretched 3-D meshes)
   if (prm.kernel != KV_AUTO)
     s->variant = prm.kernel;
+  else if (dim == 2 && precision == ISLBM_FP16NEQ)
+    s->variant = KV_TMA_R2S2;   // decoded per staged tile: pipelined kernels only
   else if (dim == 2)
     s->variant = (precision != ISLBM_FP64 && !s->uniform)
                      ? (precision == ISLBM_FP32 ? KV_TMA_R2S2 : KV_TMA_R4S2)
@@ -486,7 +557,11 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
   s->elem = precision == ISLBM_FP64 ? 8 : (precision == ISLBM_FP32 ? 4 : 2);
   s->pitch = (s->n[0] + 31) / 32 * 32;
   s->plane = (long long)s->pitch * s->n[1] * s->n[2];
-  const size_t pop_bytes = (size_t)(s->qf + s->qg) * s->plane * s->elem;
+  // FP16NEQ: 14 planes of FP16 remainders, then 4 planes of FP32 moments
+  s->state_bytes = precision == ISLBM_FP16NEQ
+                       ? (size_t)s->plane * (14 * 2 + 4 * 4)
+                       : (size_t)(s->qf + s->qg) * s->plane * s->elem;
+  const size_t pop_bytes = s->state_bytes;
   const size_t rsize = precision == ISLBM_FP64 ? 8 : 4;
   size_t tab_bytes = 0;
   for (int a = 0; a < dim; ++a) {
@@ -503,19 +578,26 @@ extern "C" islbm_status islbm_create(const double* xi_x, int nx, const double* x
     return fail(nullptr, st, m);
   };
   cudaError_t e;
+  s->mem = current_allocator();
+  auto dmalloc = [&](void** p, size_t bytes) { return dev_alloc(s->mem, p, bytes, s->stream); };
   for (int b = 0; b < 2; ++b) {
-    e = cudaMalloc(&s->buf[b], pop_bytes);
+    e = dmalloc(&s->buf[b], pop_bytes);
     if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: population buffers");
+    // pooled allocators hand back memory with old contents: start from zeros
+    // so that no step or reduction ever sees values it did not write
+    e = cudaMemsetAsync(s->buf[b], 0, pop_bytes, s->stream);
+    if (e != cudaSuccess) return cleanup(ISLBM_ERR_CUDA, "islbm_create: population buffers");
   }
-  e = cudaMalloc(&s->dtables, tab_bytes);
+  e = dmalloc(&s->dtables, tab_bytes);
   if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: tables");
-  e = cudaMalloc(&s->dscratch, (size_t)s->red_blocks * RED_STRIDE * sizeof(double));
+  e = dmalloc(reinterpret_cast<void**>(&s->dscratch),
+              (size_t)s->red_blocks * RED_STRIDE * sizeof(double));
   if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: reduction scratch");
-  e = cudaMalloc(&s->dresult, RED_STRIDE * sizeof(double));
+  e = dmalloc(reinterpret_cast<void**>(&s->dresult), RED_STRIDE * sizeof(double));
   if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: reduction result");
   e = cudaMallocHost(&s->hresult, RED_STRIDE * sizeof(double));
   if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: pinned result");
-  e = cudaMalloc(&s->derr, kDerrInts * sizeof(int));
+  e = dmalloc(reinterpret_cast<void**>(&s->derr), kDerrInts * sizeof(int));
   if (e != cudaSuccess) return cleanup(ISLBM_ERR_OOM, "islbm_create: error flag");
   e = cudaMemsetAsync(s->derr, 0, kDerrInts * sizeof(int), s->stream);
   if (e != cudaSuccess) return cleanup(ISLBM_ERR_CUDA, "islbm_create: error flag");
@@ -604,15 +686,15 @@ extern "C" void islbm_destroy(islbm_t s) {
   }
   if (s->ev_in) cudaEventDestroy(s->ev_in);
   if (s->ev_out) cudaEventDestroy(s->ev_out);
-  for (int b = 0; b < 2; ++b)
-    if (s->buf[b]) cudaFree(s->buf[b]);
-  if (s->dtables) cudaFree(s->dtables);
-  if (s->dscratch) cudaFree(s->dscratch);
-  if (s->dresult) cudaFree(s->dresult);
-  if (s->dfield) cudaFree(s->dfield);
-  if (s->derr) cudaFree(s->derr);
-  if (s->dsnap) cudaFree(s->dsnap);
-  if (s->davg) cudaFree(s->davg);
+  for (int b = 0; b < 2; ++b) dev_free(s->mem, s->buf[b], s->stream);
+  dev_free(s->mem, s->dtables, s->stream);
+  dev_free(s->mem, s->dscratch, s->stream);
+  dev_free(s->mem, s->dresult, s->stream);
+  dev_free(s->mem, s->dfield, s->stream);
+  dev_free(s->mem, s->derr, s->stream);
+  dev_free(s->mem, s->dsnap, s->stream);
+  dev_free(s->mem, s->davg, s->stream);
+  cudaStreamSynchronize(s->stream);   // the frees are stream-ordered
   if (s->hresult) cudaFreeHost(s->hresult);
   delete s;
 }
@@ -644,7 +726,7 @@ extern "C" islbm_status islbm_info(islbm_t s, islbm_info_t* o) {
   o->a_T = h.a_T;
   o->omega = h.omega;
   o->steps_per_tf = h.L / h.u_f;
-  o->bytes_per_update = 2.0 * (s->qf + s->qg) * (double)s->elem;
+  o->bytes_per_update = 2.0 * (double)s->state_bytes / (double)s->plane;
   o->time = s->time;
   o->kernel = s->variant;
   o->sm_count = s->sm_count;
@@ -659,7 +741,7 @@ static islbm_status ensure_field_buffer(Solver* s) {
   if (s->dfield) return ISLBM_OK;
   const size_t q = (size_t)(s->qf + s->qg);
   const size_t need = std::max<size_t>(5, q) * (size_t)s->nodes * sizeof(double);
-  cudaError_t e = cudaMalloc(&s->dfield, need);
+  cudaError_t e = dev_alloc(s->mem, reinterpret_cast<void**>(&s->dfield), need, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "field staging buffer");
   return ISLBM_OK;
 }
@@ -829,7 +911,7 @@ extern "C" islbm_status islbm_average_reset(islbm_t s) {
   if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_average_reset: NULL handle");
   const size_t bytes = (size_t)(s->dim + 1) * (size_t)s->nodes * sizeof(double);
   if (!s->davg) {
-    cudaError_t e = cudaMalloc(&s->davg, bytes);
+    cudaError_t e = dev_alloc(s->mem, reinterpret_cast<void**>(&s->davg), bytes, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "time-average accumulators");
   }
   CK(s, cudaMemsetAsync(s->davg, 0, bytes, s->stream));
@@ -913,7 +995,7 @@ extern "C" islbm_status islbm_steady_change(islbm_t s, double* du, double* dT) {
   if (!s || !du || !dT) return fail(s, ISLBM_ERR_ARG, "islbm_steady_change: NULL argument");
   if (!s->dsnap) {
     const size_t n = (size_t)(s->dim + 1) * (size_t)s->nodes * sizeof(double);
-    cudaError_t e = cudaMalloc(&s->dsnap, n);
+    cudaError_t e = dev_alloc(s->mem, reinterpret_cast<void**>(&s->dsnap), n, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "steady-state snapshot");
     s->snap_valid = false;
   }
@@ -1012,7 +1094,7 @@ struct CkptHeader {
 
 extern "C" islbm_status islbm_save(islbm_t s, const char* path) {
   if (!s || !path) return fail(s, ISLBM_ERR_ARG, "islbm_save: NULL argument");
-  const size_t bytes = (size_t)(s->qf + s->qg) * s->plane * s->elem;
+  const size_t bytes = s->state_bytes;
   std::vector<char> host(bytes);
   CK(s, cudaMemcpyAsync(host.data(), s->buf[s->cur], bytes, cudaMemcpyDeviceToHost, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
@@ -1034,7 +1116,7 @@ extern "C" islbm_status islbm_load(islbm_t s, const char* path) {
   FILE* fp = std::fopen(path, "rb");
   if (!fp) return fail(s, ISLBM_ERR_IO, std::string("islbm_load: cannot open ") + path);
   CkptHeader hd;
-  const size_t bytes = (size_t)(s->qf + s->qg) * s->plane * s->elem;
+  const size_t bytes = s->state_bytes;
   if (std::fread(&hd, sizeof(hd), 1, fp) != 1 || std::memcmp(hd.magic, "ISLBMCK1", 8) != 0) {
     std::fclose(fp);
     return fail(s, ISLBM_ERR_IO, "islbm_load: not a checkpoint");
@@ -1082,6 +1164,8 @@ static void drop_graphs(Solver* s) {
 extern "C" islbm_status islbm_set_row_range(islbm_t s, int row_begin, int row_end) {
   if (!s) return fail(nullptr, ISLBM_ERR_ARG, "islbm_set_row_range: NULL handle");
   if (s->dim != 2) return fail(s, ISLBM_ERR_ARG, "islbm_set_row_range: 2-D cavities only");
+  if (s->precision == ISLBM_FP16NEQ)
+    return fail(s, ISLBM_ERR_ARG, "islbm_set_row_range: not for FP16NEQ storage");
   if (row_begin < 0 || row_end > s->n[1] || row_begin >= row_end)
     return fail(s, ISLBM_ERR_ARG, "islbm_set_row_range: need 0 <= row_begin < row_end <= n_y");
   drop_graphs(s);   // captured steps carry the old range
@@ -1097,6 +1181,8 @@ extern "C" islbm_status islbm_set_row_range(islbm_t s, int row_begin, int row_en
 static islbm_status rows_args(Solver* s, int row0, int nrows, const void* p, const char* name) {
   if (!s) return fail(nullptr, ISLBM_ERR_ARG, std::string(name) + ": NULL handle");
   if (s->dim != 2) return fail(s, ISLBM_ERR_ARG, std::string(name) + ": 2-D cavities only");
+  if (s->precision == ISLBM_FP16NEQ)
+    return fail(s, ISLBM_ERR_ARG, std::string(name) + ": not for FP16NEQ storage");
   if (!p) return fail(s, ISLBM_ERR_ARG, std::string(name) + ": NULL buffer");
   if (row0 < 0 || nrows <= 0 || row0 + nrows > s->n[1])
     return fail(s, ISLBM_ERR_ARG, std::string(name) + ": rows outside the mesh");

@@ -31,6 +31,7 @@ struct islbm_batch {
   int parity = 0;                        // buffer read by the next step (all members)
   long long time = 0;
   int* derr = nullptr;
+  islbm::DevAllocator mem;               // where derr came from
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaStream_t side = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -136,7 +137,7 @@ islbm_status reactivate_all(islbm_batch* b) {
     if (b->active[i]) continue;
     islbm_t m = b->members[i];
     if (m->cur != b->parity) {
-      const size_t bytes = (size_t)(m->qf + m->qg) * (size_t)m->plane * m->elem;
+      const size_t bytes = m->state_bytes;
       const cudaError_t e = cudaMemcpyAsync(m->buf[b->parity], m->buf[m->cur], bytes,
                                             cudaMemcpyDeviceToDevice, b->stream);
       if (e != cudaSuccess)
@@ -174,7 +175,7 @@ std::map<std::tuple<int, int, long long, int>, std::vector<double>> g_tune_cache
 
 extern "C" islbm_status islbm_autotune(int n, int mesh, double a, int precision, void* stream,
                                        int* best, double* us_per_step) {
-  if (n < 4 || !best || precision < ISLBM_FP32 || precision > ISLBM_BF16DEV)
+  if (n < 4 || !best || precision < ISLBM_FP32 || precision > ISLBM_FP16NEQ)
     return bfail(nullptr, ISLBM_ERR_ARG, "islbm_autotune: n >= 4, 16/32-bit precision, best");
   const auto key = std::make_tuple(n, mesh, (long long)std::llround(a * 1e6), precision);
   std::vector<double> times;
@@ -234,7 +235,7 @@ extern "C" islbm_status islbm_batch_create(int count, const islbm_cavity* cav, i
   if (!out || !cav || count <= 0)
     return bfail(nullptr, ISLBM_ERR_ARG, "islbm_batch_create: count > 0, cavities, out");
   *out = nullptr;
-  if (precision < ISLBM_FP32 || precision > ISLBM_BF16DEV)
+  if (precision < ISLBM_FP32 || precision > ISLBM_FP16NEQ)
     return bfail(nullptr, ISLBM_ERR_ARG, "islbm_batch_create: FP32 or 16-bit storage");
   auto* b = new islbm_batch();
   b->stream = static_cast<cudaStream_t>(stream);
@@ -279,7 +280,9 @@ extern "C" islbm_status islbm_batch_create(int count, const islbm_cavity* cav, i
     b->rows.push_back(rows);
   }
   b->active.assign(b->members.size(), 1);
-  cudaError_t e = cudaMalloc(&b->derr, sizeof(int));
+  b->mem = islbm::current_allocator();
+  cudaError_t e = islbm::dev_alloc(b->mem, reinterpret_cast<void**>(&b->derr), sizeof(int),
+                                   b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->derr, 0, sizeof(int), b->stream);
   if (e == cudaSuccess) e = rebuild_groups(b);
   if (e != cudaSuccess) {
@@ -303,7 +306,8 @@ extern "C" void islbm_batch_destroy(islbm_batch_t b) {
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   for (BatchGroup* g : b->groups) delete g;
   for (islbm_t m : b->members) islbm_destroy(m);
-  if (b->derr) cudaFree(b->derr);
+  islbm::dev_free(b->mem, b->derr, b->stream);
+  if (b->stream) cudaStreamSynchronize(b->stream);
   delete b;
 }
 

@@ -41,7 +41,8 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
 __global__ void __launch_bounds__(128)
     k_gemm_bf16(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ B,
                 float* __restrict__ C, const float* __restrict__ bias, int M, int N, int K,
-                int lda, int ldb, int ldc, int transA, int transB, int accumulate, int kchunk) {
+                int lda, int ldb, int ldc, int transA, int transB, int accumulate, int kchunk,
+                float* __restrict__ partial) {
   __shared__ __nv_bfloat16 sA[GM][GK + SPAD];
   __shared__ __nv_bfloat16 sB[GN][GK + SPAD];
   const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
@@ -114,10 +115,13 @@ __global__ void __launch_bounds__(128)
         const int gn = n0 + wn + 8 * j + 2 * tig + (r & 1);
         if (gm < M && gn < N) {
           float v = acc[i][j][r];
-          if (bias && blockIdx.z == 0) v += bias[gn];
+          if (partial) {   // split K: this split's part, summed in a fixed order later
+            partial[((size_t)blockIdx.z * M + gm) * N + gn] = v;
+            continue;
+          }
+          if (bias) v += bias[gn];
           float* dst = C + (size_t)gm * ldc + gn;
-          if (gridDim.z > 1) atomicAdd(dst, v);
-          else *dst = accumulate ? *dst + v : v;
+          *dst = accumulate ? *dst + v : v;
         }
       }
 }
@@ -219,19 +223,12 @@ __global__ void k_to_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict
     y[e] = __float2bfloat16(x[e]);
 }
 
-// C[m, n] = 0 for the M x N block of a row-major matrix with leading dimension ldc
-__global__ void k_zero2d(float* __restrict__ C, int M, int N, int ldc) {
-  const long long total = (long long)M * N;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x)
-    C[(e / N) * ldc + e % N] = 0.f;
-}
-
 // Column sums of an M x N row-major matrix (bias gradients).  Block (32, 8):
-// 32 columns, 8 row lanes; each block sums a chunk of rows and adds its part
-// to out (zeroed by the caller unless accumulating).
+// 32 columns, 8 row lanes; block (x, y) sums rows [y * kColsumRows, ...) of its
+// columns into partial[y][n]; the chunks are then added in a fixed order, so
+// the sums do not depend on scheduling.
 constexpr int kColsumRows = 2048;
-__global__ void k_colsum(const float* __restrict__ x, float* __restrict__ out, int M, int N) {
+__global__ void k_colsum(const float* __restrict__ x, float* __restrict__ partial, int M, int N) {
   const int n = blockIdx.x * 32 + threadIdx.x;
   const long long m0 = (long long)blockIdx.y * kColsumRows;
   const long long m1 = m0 + kColsumRows < M ? m0 + kColsumRows : M;
@@ -245,7 +242,7 @@ __global__ void k_colsum(const float* __restrict__ x, float* __restrict__ out, i
     float t = 0.f;
 #pragma unroll
     for (int r = 0; r < 8; ++r) t += sh[r][threadIdx.x];
-    atomicAdd(out + n, t);
+    partial[(size_t)blockIdx.y * N + n] = t;
   }
 }
 
@@ -337,13 +334,11 @@ int device_sms() {
 
 }  // namespace
 
-extern "C" islbm_status islbm_cnn_gemm_bf16(const void* A, const void* B, float* C,
-                                            const float* bias, int M, int N, int K, int lda,
-                                            int ldb, int ldc, int transA, int transB,
-                                            int accumulate, void* stream) {
-  if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || ldc < N ||
-      lda < (transA ? M : K) || ldb < (transB ? K : N))
-    return ISLBM_ERR_ARG;
+namespace {
+
+islbm_status gemm_mma_sync(const void* A, const void* B, float* C, const float* bias, int M,
+                           int N, int K, int lda, int ldb, int ldc, int transA, int transB,
+                           int accumulate, void* stream) {
   const int gx = (N + GN - 1) / GN, gy = (M + GM - 1) / GM;
   // split K over blockIdx.z when the output tiles alone do not fill the GPU
   const int sms = device_sms();
@@ -356,15 +351,56 @@ extern "C" islbm_status islbm_cnn_gemm_bf16(const void* A, const void* B, float*
   }
   const int kchunk = ((K + split - 1) / split + GK - 1) / GK * GK;
   split = (K + kchunk - 1) / kchunk;
-  if (split > 1 && !accumulate) {
-    const long long n = (long long)M * N;
-    k_zero2d<<<grid_for(n), 256, 0, CNN_STREAM>>>(C, M, N, ldc);
-  }
+  float* part = nullptr;
+  if (split > 1 &&
+      islbm::cnn_splitk_workspace((size_t)split * M * N * sizeof(float), &part) != cudaSuccess)
+    return ISLBM_ERR_OOM;
   const dim3 grid(gx, gy, split);
   k_gemm_bf16<<<grid, 128, 0, CNN_STREAM>>>(static_cast<const __nv_bfloat16*>(A),
                                             static_cast<const __nv_bfloat16*>(B), C, bias, M, N,
-                                            K, lda, ldb, ldc, transA, transB, accumulate, kchunk);
+                                            K, lda, ldb, ldc, transA, transB, accumulate, kchunk,
+                                            part);
+  if (split > 1) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return launched(e);
+    return launched(
+        islbm::launch_splitk_sum(part, split, M, N, C, ldc, bias, accumulate, CNN_STREAM));
+  }
   return launched(cudaSuccess);
+}
+
+}  // namespace
+
+extern "C" islbm_status islbm_cnn_gemm_bf16_ex(const void* A, const void* B, float* C,
+                                               const float* bias, int M, int N, int K, int lda,
+                                               int ldb, int ldc, int transA, int transB,
+                                               int accumulate, int path, void* stream) {
+  if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || ldc < N ||
+      lda < (transA ? M : K) || ldb < (transB ? K : N) || path < 0 || path > 2)
+    return ISLBM_ERR_ARG;
+  const bool tc_ok = islbm::cnn_gemm_tc_supported(A, B, M, N, K, lda, ldb);
+  if (path == 2 && !tc_ok) return ISLBM_ERR_ARG;
+  if (path == 1 || !tc_ok)
+    return gemm_mma_sync(A, B, C, bias, M, N, K, lda, ldb, ldc, transA, transB, accumulate,
+                         stream);
+  return launched(islbm::launch_cnn_gemm_tc(A, B, C, bias, M, N, K, lda, ldb, ldc, transA, transB,
+                                            accumulate, CNN_STREAM, device_sms()));
+}
+
+extern "C" islbm_status islbm_cnn_gemm_bf16(const void* A, const void* B, float* C,
+                                            const float* bias, int M, int N, int K, int lda,
+                                            int ldb, int ldc, int transA, int transB,
+                                            int accumulate, void* stream) {
+  return islbm_cnn_gemm_bf16_ex(A, B, C, bias, M, N, K, lda, ldb, ldc, transA, transB,
+                                accumulate, 0, stream);
+}
+
+extern "C" islbm_status islbm_cnn_check_timeout(int reset, int* timed_out) {
+  if (!timed_out) return ISLBM_ERR_ARG;
+  const int v = islbm::cnn_tc_timeout_flag(reset);
+  if (v < 0) return ISLBM_ERR_CUDA;
+  *timed_out = v;
+  return ISLBM_OK;
 }
 
 extern "C" islbm_status islbm_cnn_im2col(const float* in, void* col, int Bn, int H, int W, int C,
@@ -418,11 +454,16 @@ extern "C" islbm_status islbm_cnn_to_bf16(const float* x, void* y, long long n, 
 extern "C" islbm_status islbm_cnn_colsum(const float* x, float* out, int M, int N, int accumulate,
                                          void* stream) {
   if (!x || !out || M <= 0 || N <= 0) return ISLBM_ERR_ARG;
-  if (!accumulate && cudaMemsetAsync(out, 0, sizeof(float) * N, CNN_STREAM) != cudaSuccess)
-    return ISLBM_ERR_CUDA;
-  const dim3 grid((N + 31) / 32, (M + kColsumRows - 1) / kColsumRows);
-  k_colsum<<<grid, dim3(32, 8), 0, CNN_STREAM>>>(x, out, M, N);
-  return launched(cudaSuccess);
+  const int chunks = (M + kColsumRows - 1) / kColsumRows;
+  float* part = nullptr;
+  if (islbm::cnn_splitk_workspace((size_t)chunks * N * sizeof(float), &part) != cudaSuccess)
+    return ISLBM_ERR_OOM;
+  const dim3 grid((N + 31) / 32, chunks);
+  k_colsum<<<grid, dim3(32, 8), 0, CNN_STREAM>>>(x, part, M, N);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return launched(e);
+  return launched(islbm::launch_splitk_sum(part, chunks, 1, N, out, N, nullptr, accumulate,
+                                           CNN_STREAM));
 }
 
 extern "C" islbm_status islbm_cnn_mse(const float* y, const float* t, const float* wc, int C,

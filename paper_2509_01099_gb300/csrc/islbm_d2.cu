@@ -51,6 +51,67 @@ __device__ __forceinline__ R wrest(int i) {
   return i == 0 ? R(4.0 / 9.0) : (i < 5 ? R(1.0 / 9.0) : R(1.0 / 36.0));
 }
 
+// Rest weights (t_0, t_i) of the D2Q5 temperature equilibrium, (1 - a_T)/5 and
+// (4 + a_T)/20.
+__device__ __forceinline__ void trest(float aT, float& t0, float& ti) {
+  t0 = (1.f - aT) * 0.2f;
+  ti = (4.f + aT) * 0.05f;
+}
+
+// The 14 stored deviations of one node (flow d_i = f_i - w_i, temperature
+// g_i), read or written as a whole: population by population, or for the
+// non-equilibrium form through its moments (islbm_store.cuh).
+template <typename S>
+struct NodeIO {
+  using R = typename Store<S>::R;
+  static __device__ __forceinline__ void load(const S* __restrict__ s, size_t idx, long long P,
+                                              float, R (&f)[9], R (&g)[5]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = Store<S>::ld(s + i * P + idx);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = Store<S>::ld(s + (9 + i) * P + idx);
+  }
+  static __device__ __forceinline__ void store(S* __restrict__ s, size_t idx, long long P, float,
+                                               const R (&f)[9], const R (&g)[5]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<S>::st(s + i * P + idx, f[i]);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Store<S>::st(s + (9 + i) * P + idx, g[i]);
+  }
+};
+
+template <>
+struct NodeIO<Neq16> {
+  static __device__ __forceinline__ void load(const Neq16* __restrict__ s, size_t idx,
+                                              long long P, float aT, float (&f)[9],
+                                              float (&g)[5]) {
+    const unsigned short* h = reinterpret_cast<const unsigned short*>(s);
+    const float* m = neq_moments(s, P);
+    unsigned short r[14];
+#pragma unroll
+    for (int i = 0; i < 14; ++i) r[i] = __ldg(h + i * P + idx);
+    float t0, ti;
+    trest(aT, t0, ti);
+    neq_decode2(__ldg(m + idx), __ldg(m + P + idx), __ldg(m + 2 * P + idx),
+                __ldg(m + 3 * P + idx), r, t0, ti, f, g);
+  }
+  static __device__ __forceinline__ void store(Neq16* __restrict__ s, size_t idx, long long P,
+                                               float aT, const float (&f)[9],
+                                               const float (&g)[5]) {
+    float t0, ti;
+    trest(aT, t0, ti);
+    float m[4];
+    unsigned short r[14];
+    neq_encode2(f, g, t0, ti, m, r);
+    unsigned short* h = reinterpret_cast<unsigned short*>(s);
+    float* mm = neq_moments(s, P);
+#pragma unroll
+    for (int i = 0; i < 14; ++i) h[i * P + idx] = r[i];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mm[k * P + idx] = m[k];
+  }
+};
+
 // MRT collision in deviation form (Sec. 2.1), of one node (L = R) or of two
 // nodes at once (L = float2, R = float: paired FP32 instructions).
 //   m = M f with the Lallemand-Luo rows (rho, e, eps, jx, qx, jy, qy, pxx, pxy);
@@ -262,11 +323,7 @@ __global__ void k_init_fields(S* __restrict__ fout, P2<typename Store<S>::R> p,
   for (int i = 1; i < 5; ++i) g[i] = ti * Tr + R(0.5) * (R(ex[i]) * ux + R(ey[i]) * uy) * T;
   R r_, a_, b_, c_;
   collide(f, g, p, r_, a_, b_, c_);
-  const size_t idx = (size_t)y * p.pitch + x;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) Store<S>::st(fout + i * p.plane + idx, f[i]);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) Store<S>::st(fout + (9 + i) * p.plane + idx, g[i]);
+  NodeIO<S>::store(fout, (size_t)y * p.pitch + x, p.plane, (float)p.a_T, f, g);
 }
 
 // Full FP64 pre-collision populations ([q][node]) -> deviations -> collision.
@@ -286,11 +343,7 @@ __global__ void k_init_pops(S* __restrict__ fout, P2<typename Store<S>::R> p,
   for (int i = 0; i < 5; ++i) g[i] = R(gin[i * nodes + node]);
   R r_, a_, b_, c_;
   collide(f, g, p, r_, a_, b_, c_);
-  const size_t idx = (size_t)y * p.pitch + x;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) Store<S>::st(fout + i * p.plane + idx, f[i]);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) Store<S>::st(fout + (9 + i) * p.plane + idx, g[i]);
+  NodeIO<S>::store(fout, (size_t)y * p.pitch + x, p.plane, (float)p.a_T, f, g);
 }
 
 // Macroscopic state of a node from the stored post-collision deviations, in
@@ -302,13 +355,15 @@ struct NodeState {
 
 template <typename S>
 __device__ __forceinline__ NodeState node_state(const S* __restrict__ s, size_t idx,
-                                                long long P, double gbeta, double Ts,
+                                                long long P, float aT, double gbeta, double Ts,
                                                 double Tref) {
+  typename Store<S>::R fr[9], gr[5];
+  NodeIO<S>::load(s, idx, P, aT, fr, gr);
   double f[9], g[5];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) f[i] = (double)Store<S>::ld(s + i * P + idx);
+  for (int i = 0; i < 9; ++i) f[i] = (double)fr[i];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) g[i] = (double)Store<S>::ld(s + (9 + i) * P + idx);
+  for (int i = 0; i < 5; ++i) g[i] = (double)gr[i];
   NodeState n;
   const double drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
   n.rho = 1.0 + drho;
@@ -328,7 +383,8 @@ __global__ void k_fields(const S* __restrict__ s, P2<typename Store<S>::R> p, do
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
-  const NodeState n = node_state(s, (size_t)y * p.pitch + x, p.plane, gbeta, Ts, Tref);
+  const NodeState n = node_state(s, (size_t)y * p.pitch + x, p.plane, (float)p.a_T, gbeta, Ts,
+                                 Tref);
   const size_t node = (size_t)y * p.nx + x;
   if (rho) rho[node] = n.rho;
   if (T) T[node] = n.T;
@@ -344,12 +400,12 @@ __global__ void k_pops(const S* __restrict__ s, P2<typename Store<S>::R> p, doub
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   const size_t nodes = (size_t)p.nx * p.ny, node = (size_t)y * p.nx + x;
-  const size_t idx = (size_t)y * p.pitch + x;
+  R fr[9], gr[5];
+  NodeIO<S>::load(s, (size_t)y * p.pitch + x, p.plane, (float)p.a_T, fr, gr);
 #pragma unroll
-  for (int i = 0; i < 9; ++i)
-    f[i * nodes + node] = (double)Store<S>::ld(s + i * p.plane + idx) + wrest<double>(i);
+  for (int i = 0; i < 9; ++i) f[i * nodes + node] = (double)fr[i] + wrest<double>(i);
 #pragma unroll
-  for (int i = 0; i < 5; ++i) g[i * nodes + node] = (double)Store<S>::ld(s + (9 + i) * p.plane + idx);
+  for (int i = 0; i < 5; ++i) g[i * nodes + node] = (double)gr[i];
 }
 
 // Population sums and velocity of one node in the compute type of the storage
@@ -365,14 +421,11 @@ struct NodeC {
 
 template <typename S>
 __device__ __forceinline__ NodeC<typename Store<S>::R> node_state_c(
-    const S* __restrict__ s, size_t idx, long long P, typename Store<S>::R gbeta,
+    const S* __restrict__ s, size_t idx, long long P, float aT, typename Store<S>::R gbeta,
     typename Store<S>::R Ts, typename Store<S>::R Tref) {
   using R = typename Store<S>::R;
   R f[9], g[5];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) f[i] = Store<S>::ld(s + i * P + idx);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) g[i] = Store<S>::ld(s + (9 + i) * P + idx);
+  NodeIO<S>::load(s, idx, P, aT, f, g);
   NodeC<R> n;
   n.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
   const R rho = R(1) + n.drho;
@@ -408,7 +461,7 @@ __global__ void __launch_bounds__(256)
   for (int y = p.y0 + (int)blockIdx.x; y < p.y1; y += (int)gridDim.x) {
     const double wy = Wy[y];
     for (int x = threadIdx.x; x < p.nx; x += blockDim.x) {
-      const NodeC<R> n = node_state_c(s, (size_t)y * p.pitch + x, p.plane, gb, ts, t0);
+      const NodeC<R> n = node_state_c(s, (size_t)y * p.pitch + x, p.plane, (float)p.a_T, gb, ts, t0);
       const double W = Wx[x] * wy;
       const R u2 = n.ux * n.ux + n.uy * n.uy;
       const R sp = sqrt(u2);
@@ -453,18 +506,26 @@ __global__ void __launch_bounds__(256)
 // sum |T*(t) - T*(t0)|, sum |T*(t0)| over the nodes, against the snapshot of
 // (u, v, T*) taken at the previous check, which is then replaced by the
 // current fields.  Partial sums per block in slots 0..3 (the others zero).
+// Without a snapshot (have_snap = 0) the old values count as zero and the
+// buffer is only written.
 template <typename S>
 __global__ void __launch_bounds__(256)
     k_steady(const S* __restrict__ s, P2<typename Store<S>::R> p, double gbeta, double Ts,
-             double T0, double dT, double* snap, double* partial) {
+             double T0, double dT, int have_snap, double* snap, double* partial) {
   double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
   const long long nodes = (long long)p.nx * p.ny;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nodes;
        k += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(k / p.nx), x = (int)(k - (long long)y * p.nx);
-    const NodeState n = node_state(s, (size_t)y * p.pitch + x, p.plane, gbeta, Ts, T0);
+    const NodeState n = node_state(s, (size_t)y * p.pitch + x, p.plane, (float)p.a_T, gbeta, Ts,
+                                   T0);
     const double Tn = (n.T - T0) / dT;
-    const double ou = snap[k], ov = snap[nodes + k], oT = snap[2 * nodes + k];
+    double ou = 0.0, ov = 0.0, oT = 0.0;
+    if (have_snap) {
+      ou = snap[k];
+      ov = snap[nodes + k];
+      oT = snap[2 * nodes + k];
+    }
     a0 += sqrt((n.ux - ou) * (n.ux - ou) + (n.uy - ov) * (n.uy - ov));
     a1 += sqrt(ou * ou + ov * ov);
     a2 += fabs(Tn - oT);
@@ -584,11 +645,12 @@ struct TileGeom {
 // packed interpolation tables (unused on a uniform mesh) come from `wxp` /
 // `wxm`, the x tables of the tile's first column, and `wyp` / `wym`, the y
 // tables of its first row (shared or global memory).
-template <typename S, int R, bool UNI>
+// O: the storage type written (S, or Neq16 when S = float holds a decoded tile).
+template <typename S, int R, bool UNI, typename O = S>
 __device__ __forceinline__ void tile_body(const S* __restrict__ sm, const float4* wxp,
                                           const float4* wxm, const float4* wyp,
                                           const float4* wym, int x0, int y0, int ry0,
-                                          S* __restrict__ fout, const P2<float>& p) {
+                                          O* __restrict__ fout, const P2<float>& p) {
   using G = TileGeom<S, R>;
   constexpr int TY = G::TY, HX = G::HX, SW = G::SW;
   const int cx0 = x0 - HX;
@@ -731,22 +793,38 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ sm, const float4
     float2 rho, ux, uy, T;
     collide(fn, gn, p, rho, ux, uy, T);
     const size_t idx = (size_t)y * p.pitch + x;
-    unsigned r = sr_seed(idx, p.step);
+    if constexpr (is_neq<O>::value) {
+      float a[9], b[5];
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-      Store<S>::st_sr(fout + (size_t)i * p.plane + idx, fn[i].x, sr_next(r));
+      for (int i = 0; i < 9; ++i) a[i] = fn[i].x;
 #pragma unroll
-    for (int i = 0; i < 5; ++i)
-      Store<S>::st_sr(fout + (size_t)(9 + i) * p.plane + idx, gn[i].x, sr_next(r));
-    if (y + 1 < p.y1) {
-      const size_t idx1 = idx + p.pitch;
-      unsigned r1 = sr_seed(idx1, p.step);
+      for (int i = 0; i < 5; ++i) b[i] = gn[i].x;
+      NodeIO<Neq16>::store(fout, idx, p.plane, p.a_T, a, b);
+      if (y + 1 < p.y1) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) a[i] = fn[i].y;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) b[i] = gn[i].y;
+        NodeIO<Neq16>::store(fout, idx + p.pitch, p.plane, p.a_T, a, b);
+      }
+    } else {
+      unsigned r = sr_seed(idx, p.step);
 #pragma unroll
       for (int i = 0; i < 9; ++i)
-        Store<S>::st_sr(fout + (size_t)i * p.plane + idx1, fn[i].y, sr_next(r1));
+        Store<S>::st_sr(fout + (size_t)i * p.plane + idx, fn[i].x, sr_next(r));
 #pragma unroll
       for (int i = 0; i < 5; ++i)
-        Store<S>::st_sr(fout + (size_t)(9 + i) * p.plane + idx1, gn[i].y, sr_next(r1));
+        Store<S>::st_sr(fout + (size_t)(9 + i) * p.plane + idx, gn[i].x, sr_next(r));
+      if (y + 1 < p.y1) {
+        const size_t idx1 = idx + p.pitch;
+        unsigned r1 = sr_seed(idx1, p.step);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          Store<S>::st_sr(fout + (size_t)i * p.plane + idx1, fn[i].y, sr_next(r1));
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+          Store<S>::st_sr(fout + (size_t)(9 + i) * p.plane + idx1, gn[i].y, sr_next(r1));
+      }
     }
   }
 }
@@ -813,11 +891,80 @@ __global__ void __launch_bounds__(kThreads, 2)
 // (x+, x- of kTX columns; y+, y- of TY rows; float4 each).
 template <typename S, int R>
 struct TmaStage {
+  using Staged = S;                                    // type of the planes the compute reads
   static constexpr unsigned PLANES = (unsigned)(14 * TileGeom<S, R>::PLANE * sizeof(S));
+  static constexpr unsigned LOADED = PLANES;           // bytes the copies bring
   static constexpr unsigned TABLES = (unsigned)((2 * kTX + 2 * TileGeom<S, R>::TY) * 16);
   static constexpr unsigned BYTES = PLANES + TABLES;
   static_assert(PLANES % 128 == 0 && BYTES % 128 == 0, "stages keep the TMA's 128-byte alignment");
 };
+
+// Non-equilibrium storage: the copies bring the FP16 remainders (box of
+// kTX + 16 columns from x0 - 8, one 16-byte chunk of halo each side) and the
+// FP32 moments (kTX + 8 columns from x0 - 4); the decode then overwrites the
+// stage with the FP32 deviations in the layout of TileGeom<float, R>, which is
+// what tile_body reads.
+template <int R>
+struct TmaStage<Neq16, R> {
+  using Staged = float;
+  using G = TileGeom<float, R>;
+  static constexpr int HW = kTX + 16;                  // remainder row width (halves)
+  static constexpr unsigned RAW_H = (unsigned)(14 * G::SH * HW * 2);
+  static constexpr unsigned RAW_M = (unsigned)(4 * G::SH * G::SW * 4);
+  static constexpr unsigned LOADED = RAW_H + RAW_M;
+  static constexpr unsigned DECODED = (unsigned)(14 * G::PLANE * 4);
+  static constexpr unsigned PLANES = ((LOADED > DECODED ? LOADED : DECODED) + 127u) / 128u * 128u;
+  static constexpr unsigned TABLES = (unsigned)((2 * kTX + 2 * G::TY) * 16);
+  static constexpr unsigned BYTES = PLANES + TABLES;
+  static_assert(RAW_H % 128 == 0 && BYTES % 128 == 0, "stages keep the TMA's 128-byte alignment");
+  static_assert(G::SW == kTX + 8, "the moment box covers the decoded window");
+};
+
+// Decode of a staged Neq16 tile in place (see TmaStage<Neq16, R>): every
+// thread first reads the remainders and moments of its nodes into registers,
+// then, after a CTA-wide barrier, writes their FP32 deviations over the stage.
+// Ends with a barrier.  Nodes outside the mesh were zero-filled by the copy and
+// decode to zero deviations, as the FP32 stage holds there.
+template <int R>
+__device__ __forceinline__ void neq_decode_tile(unsigned char* stage, float aT) {
+  using ST = TmaStage<Neq16, R>;
+  using G = typename ST::G;
+  constexpr int NODES = G::PLANE, SW = G::SW, HW = ST::HW;
+  constexpr int PER = (NODES + kThreads - 1) / kThreads;
+  static_assert(PER <= 3, "registers hold at most three nodes per thread");
+  const unsigned short* rh = reinterpret_cast<const unsigned short*>(stage);
+  const float* rm = reinterpret_cast<const float*>(stage + ST::RAW_H);
+  unsigned short r[PER][14];
+  float m[PER][4];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int n = threadIdx.x + k * kThreads;
+    if (n < NODES) {
+      const int row = n / SW, c = n - row * SW;
+#pragma unroll
+      for (int i = 0; i < 14; ++i) r[k][i] = rh[(i * G::SH + row) * HW + c + 4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) m[k][j] = rm[j * NODES + n];
+    }
+  }
+  __syncthreads();
+  float t0, ti;
+  trest(aT, t0, ti);
+  float* out = reinterpret_cast<float*>(stage);
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int n = threadIdx.x + k * kThreads;
+    if (n < NODES) {
+      float f[9], g[5];
+      neq_decode2(m[k][0], m[k][1], m[k][2], m[k][3], r[k], t0, ti, f, g);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) out[i * NODES + n] = f[i];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) out[(9 + i) * NODES + n] = g[i];
+    }
+  }
+  __syncthreads();
+}
 
 // CTAs per SM that the shared memory of a k_step_tma instantiation allows (two
 // when its ring fits in half of the 228 KB); the register budget follows.
@@ -826,13 +973,15 @@ constexpr int tma_ctas_per_sm() {
   return (size_t)STAGES * TmaStage<S, R>::BYTES + 2048 <= 114 * 1024 ? 2 : 1;
 }
 
+// tmap_m: the moment planes of a Neq16 buffer (unused for the other forms).
 template <typename S, int R, int STAGES>
 __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
-    k_step_tma(const __grid_constant__ CUtensorMap tmap, S* __restrict__ fout, P2<float> p,
-               int* sched, int dynamic) {
+    k_step_tma(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_m,
+               S* __restrict__ fout, P2<float> p, int* sched, int dynamic) {
   static_assert(STAGES >= 2, "a claimed tile is published by the barriers of the next use");
-  using G = TileGeom<S, R>;
   using ST = TmaStage<S, R>;
+  using SS = typename ST::Staged;
+  using G = TileGeom<SS, R>;
   constexpr int TY = G::TY, HX = G::HX;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)STAGES * ST::BYTES);
@@ -856,8 +1005,14 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
     const unsigned xb = 16u * (unsigned)min(kTX, p.nx - x0);
     const unsigned yb = 16u * (unsigned)min(TY, p.ny - y0);
     float4* tab = tables(st);
-    mbar_expect_tx(&bars[st], ST::PLANES + 2 * (xb + yb));
-    tma_load_3d(smem_raw + (size_t)st * ST::BYTES, &tmap, x0 - HX, ry0, 0, &bars[st]);
+    unsigned char* dst = smem_raw + (size_t)st * ST::BYTES;
+    mbar_expect_tx(&bars[st], ST::LOADED + 2 * (xb + yb));
+    if constexpr (is_neq<S>::value) {
+      tma_load_3d(dst, &tmap, x0 - 8, ry0, 0, &bars[st]);
+      tma_load_3d(dst + ST::RAW_H, &tmap_m, x0 - HX, ry0, 0, &bars[st]);
+    } else {
+      tma_load_3d(dst, &tmap, x0 - HX, ry0, 0, &bars[st]);
+    }
     bulk_load(tab, p.px[0] + x0, xb, &bars[st]);
     bulk_load(tab + kTX, p.px[1] + x0, xb, &bars[st]);
     bulk_load(tab + 2 * kTX, p.py[0] + y0, yb, &bars[st]);
@@ -871,6 +1026,8 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
   };
   if (threadIdx.x == 0) {
     asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tmap) : "memory");
+    if constexpr (is_neq<S>::value)
+      asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tmap_m) : "memory");
     for (int st = 0; st < STAGES; ++st) mbar_init(&bars[st], 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -902,10 +1059,11 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
     }
     int x0, y0, ry0;
     tile_origin(t, x0, y0, ry0);
-    const S* sm = reinterpret_cast<const S*>(smem_raw + (size_t)st * ST::BYTES);
+    if constexpr (is_neq<S>::value) neq_decode_tile<R>(smem_raw + (size_t)st * ST::BYTES, p.a_T);
+    const SS* sm = reinterpret_cast<const SS*>(smem_raw + (size_t)st * ST::BYTES);
     const float4* tab = tables(st);
-    tile_body<S, R, false>(sm, tab, tab + kTX, tab + 2 * kTX, tab + 2 * kTX + TY, x0, y0, ry0,
-                           fout, p);
+    tile_body<SS, R, false, S>(sm, tab, tab + kTX, tab + 2 * kTX, tab + 2 * kTX + TY, x0, y0,
+                               ry0, fout, p);
     __syncthreads();   // every thread is done with stage st
     if (threadIdx.x == 0) {
       if (dynamic) tile_of[st] = next;
@@ -934,6 +1092,7 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
 template <typename S>
 struct alignas(128) BatchCav {
   CUtensorMap map[2];      // descriptors of the cavity's two buffers
+  CUtensorMap mapm[2];     // Neq16: descriptors of their moment planes
   P2<float> p;
   S* out[2];               // output buffer when reading buffer 0 / 1
 };
@@ -942,9 +1101,11 @@ template <typename S, int R, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     k_step_tma_batch(const BatchCav<S>* __restrict__ cavs, const int2* __restrict__ items,
                      int nitems, int parity, unsigned step, int* err) {
-  using G = TileGeom<S, R>;
+  using ST = TmaStage<S, R>;
+  using SS = typename ST::Staged;
+  using G = TileGeom<SS, R>;
   constexpr int TY = G::TY, HX = G::HX;
-  constexpr unsigned BUF = (unsigned)(14 * G::PLANE * sizeof(S));
+  constexpr unsigned BUF = ST::PLANES;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)STAGES * BUF);
   auto origin = [&](const P2<float>& p, int t, int& x0, int& y0, int& ry0) {
@@ -959,8 +1120,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const BatchCav<S>& cv = cavs[it.x];
     int x0, y0, ry0;
     origin(cv.p, it.y, x0, y0, ry0);
-    mbar_expect_tx(&bars[st], BUF);
-    tma_load_3d(smem_raw + (size_t)st * BUF, &cv.map[parity], x0 - HX, ry0, 0, &bars[st]);
+    unsigned char* dst = smem_raw + (size_t)st * BUF;
+    mbar_expect_tx(&bars[st], ST::LOADED);
+    if constexpr (is_neq<S>::value) {
+      tma_load_3d(dst, &cv.map[parity], x0 - 8, ry0, 0, &bars[st]);
+      tma_load_3d(dst + ST::RAW_H, &cv.mapm[parity], x0 - HX, ry0, 0, &bars[st]);
+    } else {
+      tma_load_3d(dst, &cv.map[parity], x0 - HX, ry0, 0, &bars[st]);
+    }
   };
   if (threadIdx.x == 0) {
     for (int st = 0; st < STAGES; ++st) mbar_init(&bars[st], 1);
@@ -994,9 +1161,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     p.step = step;
     int x0, y0, ry0;
     origin(p, it.y, x0, y0, ry0);
-    const S* sm = reinterpret_cast<const S*>(smem_raw + (size_t)st * BUF);
-    tile_body<S, R, false>(sm, p.px[0] + x0, p.px[1] + x0, p.py[0] + y0, p.py[1] + y0, x0, y0,
-                           ry0, cv.out[parity], p);
+    if constexpr (is_neq<S>::value) neq_decode_tile<R>(smem_raw + (size_t)st * BUF, p.a_T);
+    const SS* sm = reinterpret_cast<const SS*>(smem_raw + (size_t)st * BUF);
+    tile_body<SS, R, false, S>(sm, p.px[0] + x0, p.px[1] + x0, p.py[0] + y0, p.py[1] + y0, x0,
+                               y0, ry0, cv.out[parity], p);
     __syncthreads();
     if (threadIdx.x == 0) {
       const int in = i + STAGES * gridDim.x;
@@ -1032,7 +1200,7 @@ constexpr int kDynamicTilesPerCta = 24;
 
 template <typename S, int R, int STAGES>
 cudaError_t launch_tma(const Solver& s, int cur, S* out, const P2<float>& p) {
-  using G = TileGeom<S, R>;
+  using G = TileGeom<typename TmaStage<S, R>::Staged, R>;
   constexpr size_t smem = (size_t)STAGES * TmaStage<S, R>::BYTES + 64;
   int blocks_per_sm = 0;
   const cudaError_t e = launch_setup_once(
@@ -1052,7 +1220,8 @@ cudaError_t launch_tma(const Solver& s, int cur, S* out, const P2<float>& p) {
   // claimed tiles pay off once a CTA walks more than a few dozen tiles
   const int dynamic = ntiles >= kDynamicTilesPerCta * grid ? 1 : 0;
   k_step_tma<S, R, STAGES><<<grid, kThreads, smem, s.stream>>>(
-      *reinterpret_cast<const CUtensorMap*>(s.tmap[cur]), out, p, s.derr, dynamic);
+      *reinterpret_cast<const CUtensorMap*>(s.tmap[cur]),
+      *reinterpret_cast<const CUtensorMap*>(s.tmap_m[cur]), out, p, s.derr, dynamic);
   return cudaGetLastError();
 }
 
@@ -1068,6 +1237,7 @@ cudaError_t dispatch(Solver& s, A... a) {
     case ISLBM_FP32: return Fn<float>::run(s, a...);
     case ISLBM_FP16DEV: return Fn<__half>::run(s, a...);
     case ISLBM_BF16DEV: return Fn<__nv_bfloat16>::run(s, a...);
+    case ISLBM_FP16NEQ: return Fn<Neq16>::run(s, a...);
   }
   return cudaErrorInvalidValue;
 }
@@ -1077,27 +1247,36 @@ struct StepFn {
   static cudaError_t run(Solver& s) {
     using R = typename Store<S>::R;
     const P2<R> p = make_params<R>(s);
-    const S* in = static_cast<const S*>(s.buf[s.cur]);
     S* out = static_cast<S*>(s.buf[s.cur ^ 1]);
-    if constexpr (!std::is_same<S, double>::value) {
-      // the tiled kernels cover the centred stencil (their halo is one node);
-      // on the uniform mesh the direct pure-shift kernel is the default
-      if (s.stencil == ISLBM_STENCIL_CENTRED) {
-        switch (s.variant) {
-          case KV_TILED: return launch_tiled<S, 4, false>(s, in, out, p);
-          case KV_TMA_R4S2: return launch_tma<S, 4, 2>(s, s.cur, out, p);
-          case KV_TMA_R2S2: return launch_tma<S, 2, 2>(s, s.cur, out, p);
-          case KV_TMA_R2S3: return launch_tma<S, 2, 3>(s, s.cur, out, p);
-          case KV_TMA_R4S3: return launch_tma<S, 4, 3>(s, s.cur, out, p);
-          default: break;
+    if constexpr (is_neq<S>::value) {
+      // the non-equilibrium form is decoded per staged tile: pipelined kernels only
+      switch (s.variant) {
+        case KV_TMA_R2S2: return launch_tma<S, 2, 2>(s, s.cur, out, p);
+        case KV_TMA_R2S3: return launch_tma<S, 2, 3>(s, s.cur, out, p);
+        default: return cudaErrorInvalidValue;
+      }
+    } else {
+      const S* in = static_cast<const S*>(s.buf[s.cur]);
+      if constexpr (!std::is_same<S, double>::value) {
+        // the tiled kernels cover the centred stencil (their halo is one node);
+        // on the uniform mesh the direct pure-shift kernel is the default
+        if (s.stencil == ISLBM_STENCIL_CENTRED) {
+          switch (s.variant) {
+            case KV_TILED: return launch_tiled<S, 4, false>(s, in, out, p);
+            case KV_TMA_R4S2: return launch_tma<S, 4, 2>(s, s.cur, out, p);
+            case KV_TMA_R2S2: return launch_tma<S, 2, 2>(s, s.cur, out, p);
+            case KV_TMA_R2S3: return launch_tma<S, 2, 3>(s, s.cur, out, p);
+            case KV_TMA_R4S3: return launch_tma<S, 4, 3>(s, s.cur, out, p);
+            default: break;
+          }
         }
       }
+      if (s.uniform)
+        k_step<S, true><<<grid2_step(s), block2(), 0, s.stream>>>(in, out, p);
+      else
+        k_step<S, false><<<grid2_step(s), block2(), 0, s.stream>>>(in, out, p);
+      return cudaGetLastError();
     }
-    if (s.uniform)
-      k_step<S, true><<<grid2_step(s), block2(), 0, s.stream>>>(in, out, p);
-    else
-      k_step<S, false><<<grid2_step(s), block2(), 0, s.stream>>>(in, out, p);
-    return cudaGetLastError();
   }
 };
 
@@ -1160,7 +1339,7 @@ struct SteadyFn {
     using R = typename Store<S>::R;
     k_steady<S><<<s.red_blocks, 256, 0, s.stream>>>(
         static_cast<const S*>(s.buf[s.cur]), make_params<R>(s), s.ph.gbeta, s.ph.Ts, s.ph.T0,
-        s.ph.dT, s.dsnap, s.dscratch);
+        s.ph.dT, s.snap_valid ? 1 : 0, s.dsnap, s.dscratch);
     return cudaGetLastError();
   }
 };
@@ -1222,9 +1401,12 @@ struct BatchGroupImpl : BatchGroup {
   int2* ditems = nullptr;
   int ncav = 0, nitems = 0, grid = 0;
   size_t smem = 0;
+  DevAllocator mem;
+  cudaStream_t stream = nullptr;
   ~BatchGroupImpl() override {
-    if (dcavs) cudaFree(dcavs);
-    if (ditems) cudaFree(ditems);
+    dev_free(mem, dcavs, stream);
+    dev_free(mem, ditems, stream);
+    cudaStreamSynchronize(stream);
   }
   cudaError_t launch(cudaStream_t st, int parity, unsigned step, int* err) override {
     k_step_tma_batch<S, R, 2><<<grid, kThreads, smem, st>>>(dcavs, ditems, nitems, parity, step,
@@ -1236,9 +1418,9 @@ struct BatchGroupImpl : BatchGroup {
 template <typename S, int R>
 cudaError_t make_group_impl(const std::vector<Solver*>& members, int sm_count,
                             cudaStream_t stream, BatchGroup** out) {
-  using G = TileGeom<S, R>;
+  using G = TileGeom<typename TmaStage<S, R>::Staged, R>;
   auto* g = new BatchGroupImpl<S, R>();
-  g->smem = (size_t)2 * 14 * G::PLANE * sizeof(S) + 64;
+  g->smem = (size_t)2 * TmaStage<S, R>::PLANES + 64;
   cudaError_t e = cudaFuncSetAttribute(k_step_tma_batch<S, R, 2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem);
   int bps = 0;
@@ -1251,6 +1433,8 @@ cudaError_t make_group_impl(const std::vector<Solver*>& members, int sm_count,
     Solver& m = *members[c];
     std::memcpy(&cavs[c].map[0], m.tmap[0], sizeof(CUtensorMap));
     std::memcpy(&cavs[c].map[1], m.tmap[1], sizeof(CUtensorMap));
+    std::memcpy(&cavs[c].mapm[0], m.tmap_m[0], sizeof(CUtensorMap));
+    std::memcpy(&cavs[c].mapm[1], m.tmap_m[1], sizeof(CUtensorMap));
     cavs[c].p = make_params<float>(m);
     cavs[c].out[0] = static_cast<S*>(m.buf[1]);
     cavs[c].out[1] = static_cast<S*>(m.buf[0]);
@@ -1260,8 +1444,14 @@ cudaError_t make_group_impl(const std::vector<Solver*>& members, int sm_count,
   g->ncav = (int)members.size();
   g->nitems = (int)items.size();
   g->grid = std::max(1, std::min(g->nitems, sm_count * std::max(bps, 1)));
-  if (e == cudaSuccess) e = cudaMalloc(&g->dcavs, cavs.size() * sizeof(BatchCav<S>));
-  if (e == cudaSuccess) e = cudaMalloc(&g->ditems, items.size() * sizeof(int2));
+  g->mem = current_allocator();
+  g->stream = stream;
+  if (e == cudaSuccess)
+    e = dev_alloc(g->mem, reinterpret_cast<void**>(&g->dcavs), cavs.size() * sizeof(BatchCav<S>),
+                  stream);
+  if (e == cudaSuccess)
+    e = dev_alloc(g->mem, reinterpret_cast<void**>(&g->ditems), items.size() * sizeof(int2),
+                  stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(g->dcavs, cavs.data(), cavs.size() * sizeof(BatchCav<S>),
                         cudaMemcpyHostToDevice, stream);
@@ -1284,6 +1474,9 @@ cudaError_t make_group_r(const std::vector<Solver*>& m, int precision, int sm, c
     case ISLBM_FP32: return make_group_impl<float, R>(m, sm, st, out);
     case ISLBM_FP16DEV: return make_group_impl<__half, R>(m, sm, st, out);
     case ISLBM_BF16DEV: return make_group_impl<__nv_bfloat16, R>(m, sm, st, out);
+    case ISLBM_FP16NEQ:
+      if constexpr (R == 2) return make_group_impl<Neq16, R>(m, sm, st, out);
+      break;
   }
   return cudaErrorInvalidValue;
 }

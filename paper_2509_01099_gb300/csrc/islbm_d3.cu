@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(256)
 template <typename S>
 __global__ void __launch_bounds__(256)
     k_steady3(const S* __restrict__ s, P3<typename Store<S>::R> p, double gbeta, double Ts,
-              double T0, double dT, double* snap, double* partial) {
+              double T0, double dT, int have_snap, double* snap, double* partial) {
   double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
   const long long nodes = (long long)p.nx * p.ny * p.nz;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nodes;
@@ -374,8 +374,13 @@ __global__ void __launch_bounds__(256)
     const NodeState3 n =
         node_state3(s, ((size_t)z * p.ny + y) * p.pitch + x, p.plane, gbeta, Ts, T0);
     const double Tn = (n.T - T0) / dT;
-    const double ou = snap[k], ov = snap[nodes + k], ow = snap[2 * nodes + k];
-    const double oT = snap[3 * nodes + k];
+    double ou = 0.0, ov = 0.0, ow = 0.0, oT = 0.0;
+    if (have_snap) {
+      ou = snap[k];
+      ov = snap[nodes + k];
+      ow = snap[2 * nodes + k];
+      oT = snap[3 * nodes + k];
+    }
     a0 += sqrt((n.ux - ou) * (n.ux - ou) + (n.uy - ov) * (n.uy - ov) + (n.uz - ow) * (n.uz - ow));
     a1 += sqrt(ou * ou + ov * ov + ow * ow);
     a2 += fabs(Tn - oT);
@@ -486,7 +491,7 @@ struct Steady3 {
     using R = typename Store<S>::R;
     k_steady3<S><<<s.red_blocks, 256, 0, s.stream>>>(
         static_cast<const S*>(s.buf[s.cur]), make_params3<R>(s), s.ph.gbeta, s.ph.Ts, s.ph.T0,
-        s.ph.dT, s.dsnap, s.dscratch);
+        s.ph.dT, s.snap_valid ? 1 : 0, s.dsnap, s.dscratch);
     return cudaGetLastError();
   }
 };

@@ -36,6 +36,19 @@ int bounds_flag_d2(int reset);
 int bounds_flag_d3(int reset);
 int bounds_flag_zm(int reset);
 
+// Device memory of the library: through the allocator registered with
+// islbm_set_allocator, else cudaMallocAsync / cudaFreeAsync on the stream of
+// the owner.  An owner records the allocator its memory came from (a later
+// registration does not change how that memory is freed).
+struct DevAllocator {
+  islbm_alloc_fn alloc = nullptr;
+  islbm_free_fn release = nullptr;
+  void* ctx = nullptr;
+};
+DevAllocator current_allocator();
+cudaError_t dev_alloc(const DevAllocator& a, void** p, size_t bytes, cudaStream_t stream);
+void dev_free(const DevAllocator& a, void* p, cudaStream_t stream);
+
 // One-time launch setup of a kernel (shared-memory attribute, occupancy query),
 // run once per (kernel, current device) under a lock; *value receives what the
 // setup stored (e.g. CTAs per SM).
@@ -125,7 +138,8 @@ struct Solver {
   bool uniform = false;
   cudaStream_t stream = nullptr;
   int device = 0;
-  size_t elem = 4;          // bytes per stored population value
+  size_t elem = 4;          // bytes per stored population value (FP16NEQ: per remainder)
+  size_t state_bytes = 0;   // bytes of one state buffer
   int pitch = 0;            // x pitch in elements
   long long plane = 0;      // elements per population plane
   long long nodes = 0;
@@ -146,6 +160,7 @@ struct Solver {
   long long avg_count = 0;        // states accumulated since the last reset
   bool snap_valid = false;
   std::string err;
+  DevAllocator mem;               // where this handle's device memory comes from
   unsigned long long fingerprint = 0;
   int variant = KV_DIRECT;        // step kernel of the 2-D FP32/16-bit path
   // 2-D slab of a domain decomposition: steps and reductions cover rows
@@ -156,6 +171,7 @@ struct Solver {
   // [2] CTAs finished (the 2-D TMA kernel's dynamic schedule; zero between launches)
   int* derr = nullptr;
   alignas(128) unsigned char tmap[2][128];   // TMA descriptors of buf[0] / buf[1]
+  alignas(128) unsigned char tmap_m[2][128]; // FP16NEQ: of their moment planes
   alignas(128) unsigned char tmap3[2][7][128];   // 3-D: one descriptor per box shape
   // CUDA graphs of kGraphSteps steps, one per starting buffer, replayed on a
   // private stream that is ordered against `stream` with events
@@ -217,6 +233,19 @@ cudaError_t launch_steady_3d(Solver& s);
 }  // namespace islbm
 
 namespace islbm {
+// tcgen05 GEMM of the warm-start network (islbm_cnn_tc.cu)
+bool cnn_gemm_tc_supported(const void* A, const void* B, int M, int N, int K, int lda, int ldb);
+cudaError_t launch_cnn_gemm_tc(const void* A, const void* B, float* C, const float* bias, int M,
+                               int N, int K, int lda, int ldb, int ldc, int transA, int transB,
+                               int accumulate, cudaStream_t stream, int sms);
+// the tcgen05 GEMM's timeout flag (-1: not readable); reset != 0 clears it
+int cnn_tc_timeout_flag(int reset);
+// split-K partial tiles of the network GEMMs: a per-device workspace grown on
+// demand, and the fixed-order sum of the partials into C
+cudaError_t cnn_splitk_workspace(size_t bytes, float** out);
+cudaError_t launch_splitk_sum(const float* partial, int split, int M, int N, float* C, int ldc,
+                              const float* bias, int accumulate, cudaStream_t stream);
+
 // One launch configuration of the batched step: the cavities sharing a tile
 // height, with their device-side parameter records and work list.
 struct BatchGroup {

@@ -29,7 +29,9 @@ __global__ void k_wait_never(int* err) {
 extern "C" islbm_status islbm_selftest_wait_timeout(void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int* d = nullptr;
-  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return ISLBM_ERR_OOM;
+  const islbm::DevAllocator mem = islbm::current_allocator();
+  if (islbm::dev_alloc(mem, reinterpret_cast<void**>(&d), sizeof(int), st) != cudaSuccess)
+    return ISLBM_ERR_OOM;
   int flag = 0;
   cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), st);
   if (e == cudaSuccess) {
@@ -38,7 +40,8 @@ extern "C" islbm_status islbm_selftest_wait_timeout(void* stream) {
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, d, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(d);
+  islbm::dev_free(mem, d, st);
+  cudaStreamSynchronize(st);
   if (e != cudaSuccess) return ISLBM_ERR_CUDA;
   return flag ? ISLBM_ERR_TIMEOUT : ISLBM_OK;
 }

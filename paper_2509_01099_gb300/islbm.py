@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 LATTICES = {"d2q9_d2q5": 0, "d3q19_d3q7": 1}
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp16dev": 2, "bf16dev": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp16dev": 2, "bf16dev": 3, "fp16neq": 4}
 STENCILS = {"centred": 0, "upwind": 1}
 REFERENCES = {"mean": 0, "cold": 1}
 KERNEL_VARIANTS = 10     # ISLBM_KERNEL_VARIANTS of include/islbm.h
@@ -41,7 +41,8 @@ EXPORTS = (
     "islbm_cnn_upsample2x", "islbm_cnn_tanh", "islbm_cnn_tanh_back", "islbm_cnn_to_bf16",
     "islbm_cnn_colsum", "islbm_cnn_mse", "islbm_cnn_adam", "islbm_cnn_pack_fields",
     "islbm_cnn_unpack_fields", "islbm_set_row_range", "islbm_get_rows", "islbm_set_rows",
-    "islbm_reduce_sums", "islbm_finish_sums",
+    "islbm_reduce_sums", "islbm_finish_sums", "islbm_cnn_gemm_bf16_ex", "islbm_cnn_check_timeout",
+    "islbm_set_allocator",
 )
 REDUCTION_SUMS = 16     # ISLBM_REDUCTION_SUMS of include/islbm.h
 SUM_MAX_SLOT = 13       # ISLBM_SUM_MAX_SLOT: the one partial combined by max
@@ -96,6 +97,56 @@ def library_path() -> str:
     """The library to load: $ISLBM_LIBRARY if set (e.g. the bounds-checked
     build), else the in-tree libislbm.so."""
     return os.environ.get("ISLBM_LIBRARY") or _build.LIB
+
+
+# device-memory callbacks of islbm_set_allocator
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
+                            ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+# Every callback ever registered stays referenced for the life of the process:
+# handles (and the network's workspace) keep the allocator they were created
+# with and call its release function when they are destroyed, possibly after
+# another allocator has been registered.
+_allocator_refs = []
+
+
+def islbm_set_allocator(alloc=None, release=None):
+    """Register Python callables alloc(nbytes, device, stream) -> int pointer and
+    release(ptr, device, stream) as the library's device allocator (None, None:
+    back to cudaMallocAsync on the owner's stream)."""
+    lib = load_library()
+    if alloc is None and release is None:
+        _check(lib.islbm_set_allocator(ALLOC_FN(), FREE_FN(), None))
+        return
+
+    def _a(nbytes, device, stream, ctx):
+        try:
+            return int(alloc(int(nbytes), int(device), int(stream or 0))) or None
+        except Exception:     # noqa: BLE001 - a NULL return is the library's OOM
+            return None
+
+    def _r(ptr, device, stream, ctx):
+        try:
+            release(int(ptr), int(device), int(stream or 0))
+        except Exception:     # noqa: BLE001
+            pass
+
+    fa, fr = ALLOC_FN(_a), FREE_FN(_r)
+    _allocator_refs.extend([fa, fr, _a, _r])
+    _check(lib.islbm_set_allocator(fa, fr, None))
+
+
+def torch_allocator():
+    """(alloc, release) on torch's CUDA caching allocator."""
+    import torch
+
+    def alloc(nbytes, device, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, device=device, stream=stream)
+
+    def release(ptr, device, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return alloc, release
 
 
 def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
@@ -155,6 +206,8 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
         "islbm_batch_run_to_steady": (i, [h, d, ctypes.c_longlong, ctypes.c_longlong,
                                           P(ctypes.c_longlong)]),
         "islbm_cnn_gemm_bf16": (i, [vp, vp, vp, vp, i, i, i, i, i, i, i, i, i, vp]),
+        "islbm_cnn_gemm_bf16_ex": (i, [vp, vp, vp, vp, i, i, i, i, i, i, i, i, i, i, vp]),
+        "islbm_cnn_check_timeout": (i, [i, P(i)]),
         "islbm_cnn_im2col": (i, [vp, vp, i, i, i, i, i, vp]),
         "islbm_cnn_col2im": (i, [vp, vp, i, i, i, i, i, vp]),
         "islbm_cnn_upsample2x": (i, [vp, vp, i, i, i, i, i, vp]),
@@ -170,6 +223,7 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
                                ctypes.c_longlong, vp]),
         "islbm_run_to_steady": (i, [h, d, ctypes.c_longlong, ctypes.c_longlong,
                                     P(ctypes.c_longlong), dp, dp]),
+        "islbm_set_allocator": (i, [ALLOC_FN, FREE_FN, vp]),
         "islbm_set_row_range": (i, [h, i, i]),
         "islbm_get_rows": (i, [h, i, i, vp]),
         "islbm_set_rows": (i, [h, i, i, vp]),
@@ -181,6 +235,15 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
         fn.restype = res
         fn.argtypes = args
     _lib = lib
+    # the library's device memory comes from torch's caching allocator when
+    # torch has CUDA (else cudaMallocAsync on the owner's stream);
+    # ISLBM_TORCH_ALLOCATOR=0 keeps the library's own default
+    try:
+        import torch
+        if torch.cuda.is_available() and os.environ.get("ISLBM_TORCH_ALLOCATOR", "1") != "0":
+            islbm_set_allocator(*torch_allocator())
+    except ImportError:
+        pass
     return lib
 
 

@@ -126,3 +126,35 @@ def test_noalloc_binding_rejects_bad_tensors_before_any_launch():
             pkg.islbm_reduce_noalloc(args[0], args[1], nx, ny, args[2], args[3], 1e6, 0.71)
     with pytest.raises(TypeError):
         pkg.islbm_reduce_noalloc([0.0], ok_g, nx, ny, xi, xi, 1e6, 0.71)
+
+
+def test_allocator_registration_without_a_gpu():
+    """islbm_set_allocator takes both callbacks or neither; registering does
+    not touch the device."""
+    import paper_2509_01099_gb300 as pkg
+    from paper_2509_01099_gb300 import islbm as I
+    lib = pkg.load_library()
+    calls = []
+    pkg.islbm_set_allocator(lambda n, d, s: calls.append(n) or 0, lambda p, d, s: None)
+    assert calls == []
+    # one function alone is an argument error
+    assert lib.islbm_set_allocator(I.ALLOC_FN(lambda *a: None), I.FREE_FN(), None) != 0
+    pkg.islbm_set_allocator(None, None)
+    # every callback ever registered stays referenced (handles keep theirs)
+    assert len(I._allocator_refs) >= 2
+
+
+def test_fp16neq_needs_the_2d_pipelined_kernels(lib):
+    """The non-equilibrium storage is decoded per staged tile: only the 2-D
+    pipelined kernels with 8-row tiles run it.  Every other choice is refused
+    before a device is touched."""
+    xi = O.mesh_tanh(16, 1.5)
+    cases = [dict(xi_z=xi), dict(kernel=1), dict(kernel=2), dict(kernel=3), dict(kernel=6),
+             dict(stencil=1)]
+    for kw in cases:
+        p = pkg.islbm_default_params()
+        p.kernel = kw.get("kernel", 0)
+        p.stencil = kw.get("stencil", 0)
+        with pytest.raises(pkg.IslbmError) as e:
+            pkg.islbm_create(xi, xi, kw.get("xi_z"), 1e6, 0.71, None, "fp16neq", p, None)
+        assert e.value.status == 1, kw

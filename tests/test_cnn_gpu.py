@@ -83,6 +83,88 @@ def test_gemm_bf16_matches_float64_of_rounded_operands(M, N, K, ta, tb):
         assert err.max() < 1e-5, err.max()
 
 
+def _gemm_case(M, N, K, ta, tb, seed, path, acc=0, lda_pad=0, ldb_pad=0):
+    """One product through islbm_cnn_gemm_bf16_ex; returns (C, reference, scale)."""
+    torch = _torch()
+    ashape = (K, M + lda_pad) if ta else (M, K + lda_pad)
+    bshape = (N, K + ldb_pad) if tb else (K, N + ldb_pad)
+    g = gaussian_arrays([("A", ashape), ("B", bshape), ("bias", (N,)), ("C0", (M, N))],
+                        seed=seed)
+    A = torch.from_numpy(g["A"].astype(np.float32)).cuda().to(torch.bfloat16)
+    B = torch.from_numpy(g["B"].astype(np.float32)).cuda().to(torch.bfloat16)
+    bias = torch.from_numpy(g["bias"].astype(np.float32)).cuda()
+    C = torch.from_numpy(g["C0"].astype(np.float32)).cuda()
+    lda, ldb = A.shape[1], B.shape[1]
+    st = _lib().islbm_cnn_gemm_bf16_ex(_p(A), _p(B), _p(C), _p(bias), M, N, K, lda, ldb, N,
+                                       ta, tb, acc, path, _stream())
+    assert st == 0
+    torch.cuda.synchronize()
+    Ar, Br = _bf16_round(g["A"]), _bf16_round(g["B"])
+    opA = Ar[:, :M].T if ta else Ar[:, :K]
+    opB = Br[:, :K].T if tb else Br[:, :N]
+    ref = opA @ opB + g["bias"].astype(np.float32) + (g["C0"].astype(np.float32) if acc else 0)
+    scale = np.abs(opA) @ np.abs(opB) + np.abs(g["bias"]) + (np.abs(g["C0"]) if acc else 0)
+    return C.cpu().numpy(), ref, scale
+
+
+# Shapes of the tcgen05 path: every N tile width (16 .. 256, ragged N), ragged M
+# and K ends (a k stage cut inside its 64 values, K below one stage), all four
+# operand orientations, the network's own products (forward im2col x W, data
+# gradient dY x W^T, weight gradient col^T x dY over 256^2 x 16 nodes), padded
+# leading dimensions, bias and accumulation.
+TC_CASES = [
+    (128, 16, 64, 0, 0), (200, 3, 40, 0, 1), (256, 32, 576, 0, 0), (300, 48, 432, 0, 0),
+    (1000, 64, 144, 0, 0), (129, 100, 70, 1, 0), (96, 128, 24, 0, 1), (64, 200, 200, 1, 1),
+    (517, 256, 136, 0, 1), (130, 600, 96, 0, 1),
+    (65536, 16, 144, 0, 0),        # forward of the last 3x3 stage at 256^2 (one sample)
+    (16384, 576, 64, 0, 1),        # data gradient dY W^T of a 64-channel stage
+    (576, 64, 65536, 1, 0),        # weight gradient col^T dY: split over K
+    (16, 4096, 256, 0, 0),         # the second fully connected layer (16 samples)
+]
+
+
+@pytest.mark.parametrize("M,N,K,ta,tb", TC_CASES)
+def test_gemm_tcgen05_matches_float64_of_rounded_operands(M, N, K, ta, tb):
+    # leading dimensions rounded up to 8 elements (the path's condition), then
+    # a further padding of one and two chunks
+    la, lb = (M if ta else K), (K if tb else N)
+    base = ((-la) % 8, (-lb) % 8)
+    for acc, extra in ((0, (0, 0)), (1, (8, 16))):
+        C, ref, scale = _gemm_case(M, N, K, ta, tb, seed=M + 3 * N + 7 * K + ta + 2 * tb,
+                                   path=2, acc=acc, lda_pad=base[0] + extra[0],
+                                   ldb_pad=base[1] + extra[1])
+        err = np.abs(C - ref) / scale
+        assert err.max() < 1e-5, (acc, err.max())
+    flag = ctypes.c_int(-1)
+    assert _lib().islbm_cnn_check_timeout(1, ctypes.byref(flag)) == 0 and flag.value == 0
+
+
+def test_gemm_split_k_is_deterministic_on_both_paths():
+    """The weight-gradient shape (split over K): two runs of either path give
+    the same bits (the splits are added in a fixed order); the paths agree
+    within the accumulation tolerance."""
+    a, ref, scale = _gemm_case(576, 64, 65536, 1, 0, seed=5, path=2)
+    b, _, _ = _gemm_case(576, 64, 65536, 1, 0, seed=5, path=2)
+    c, _, _ = _gemm_case(576, 64, 65536, 1, 0, seed=5, path=1)
+    d, _, _ = _gemm_case(576, 64, 65536, 1, 0, seed=5, path=1)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(c, d)
+    assert (np.abs(a - c) / scale).max() < 2e-5
+
+
+def test_gemm_tcgen05_refuses_unaligned_operands():
+    torch = _torch()
+    lib = _lib()
+    A = torch.zeros(4096, dtype=torch.bfloat16, device="cuda")
+    C = torch.zeros(4096, device="cuda")
+    # lda = 37 is not a multiple of 8 elements: path 2 refuses, path 0 takes mma.sync
+    assert lib.islbm_cnn_gemm_bf16_ex(_p(A), _p(A), _p(C), None, 8, 8, 37, 37, 8, 8, 0, 0, 0, 2,
+                                      _stream()) != 0
+    assert lib.islbm_cnn_gemm_bf16_ex(_p(A), _p(A), _p(C), None, 8, 8, 37, 37, 8, 8, 0, 0, 0, 0,
+                                      _stream()) == 0
+    torch.cuda.synchronize()
+
+
 def test_gemm_rejects_bad_sizes():
     torch = _torch()
     lib = _lib()
@@ -135,8 +217,12 @@ def test_im2col_col2im_upsample_colsum():
     out = torch.full((37,), 5.0, device="cuda")
     assert lib.islbm_cnn_colsum(_p(bt), _p(out), 10000, 37, 0, _stream()) == 0
     np.testing.assert_allclose(out.cpu().numpy(), big.sum(axis=0), rtol=0, atol=2e-3)
+    first = out.cpu().numpy().copy()
     assert lib.islbm_cnn_colsum(_p(bt), _p(out), 10000, 37, 1, _stream()) == 0
     np.testing.assert_allclose(out.cpu().numpy(), 2 * big.sum(axis=0), rtol=0, atol=4e-3)
+    # the row chunks are added in a fixed order: a repeat gives the same bits
+    assert lib.islbm_cnn_colsum(_p(bt), _p(out), 10000, 37, 0, _stream()) == 0
+    np.testing.assert_array_equal(out.cpu().numpy(), first)
 
 
 def test_mse_tanh_adam_against_oracle():

@@ -8,7 +8,9 @@ linearly in the number of steps from the 1e-12-level seen after 1000 steps,
 so 1e-9 field-relative.  FP32: 1e-5 after 1000 steps grows to at most ~1e-4.
 FP16 / BF16 deviations (stochastically rounded, unit roundoff 2^-11 / 2^-8 of
 values ~1e-2): the fields are checked at 2e-2 / 1e-1 and Nu at 2% / 5%; the
-measured errors are printed for the record.
+measured errors are printed for the record.  FP16NEQ (FP32 moments, FP16
+remainders at least ten times smaller than the deviations) is held to the
+FP16 bounds.
 """
 import functools
 
@@ -27,8 +29,8 @@ if gpu_available():
 import paper_2509_01099_gb300 as pkg  # noqa: E402
 
 N, STEPS, RA = 64, 20_000, 1e6
-FIELD_TOL = {"fp64": 1e-9, "fp32": 1e-4, "fp16dev": 2e-2, "bf16dev": 1e-1}
-NU_TOL = {"fp64": 1e-9, "fp32": 1e-4, "fp16dev": 2e-2, "bf16dev": 5e-2}
+FIELD_TOL = {"fp64": 1e-9, "fp32": 1e-4, "fp16dev": 2e-2, "bf16dev": 1e-1, "fp16neq": 2e-2}
+NU_TOL = {"fp64": 1e-9, "fp32": 1e-4, "fp16dev": 2e-2, "bf16dev": 5e-2, "fp16neq": 2e-2}
 
 
 @functools.lru_cache(maxsize=None)
@@ -41,7 +43,7 @@ def oracle_state():
     return T, u, cav.reductions()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16dev", "bf16dev"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16dev", "bf16dev", "fp16neq"])
 def test_n64_workload_against_oracle(precision):
     T, u, red_ref = oracle_state()
     xi = pkg.islbm_mesh_tanh(N, 1.5)
