@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "ISLBM MLUPS & %HBM roofline; wall time to steady Nu, plain vs mixed/learned"
 WORKLOAD = "2-D side-heated cavity, D2Q9+D2Q5, Ra=1e8, Pr=0.71, 1024x1024 tanh-stretched mesh (a=1.5)"
 BYTES_PER_VALUE = {"fp64": 8, "fp32": 4, "fp16dev": 2, "bf16dev": 2, "fp16neq": 2}
-DTYPE = {"fp64": "f64", "fp32": "f32", "fp16dev": "f16", "bf16dev": "bf16"}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16dev": "f16", "bf16dev": "bf16", "fp16neq": "f32+f16"}
 
 
 def parse():
@@ -84,6 +84,9 @@ def parse():
                     help="mesh sizes of --grid-study, coarse to fine")
     ap.add_argument("--batch", action="store_true",
                     help="64-cavity Ra sweep: batched persistent launch vs a per-cavity loop")
+    ap.add_argument("--cnn-gemm", action="store_true",
+                    help="the warm-start network's GEMM shapes (batch 16) on the tcgen05 and "
+                         "mma.sync paths: device time, TFLOP/s, GB/s")
     args = ap.parse_args()
     if args.Ra is None:
         args.Ra = 1e8 if args.dim == 2 else 1e7
@@ -816,8 +819,9 @@ PAPER_STEADY = {
 def steady_run(pkg, torch, dim, n, Ra, init, tol, max_steps):
     """One erf-mesh cavity (a = 1.5, FP32) from `init` (None: rest with the seeded
     noise; else fields T, u, v[, w]) to a steady state: in 2-D the Nu-window
-    criterion (100 samples 1000 steps apart), in 3-D the field criterion of
-    Sec. 3 over 2000 steps.  Returns the reductions, centre values and fields."""
+    criterion (100 samples 1000 steps apart), then the integral quantities
+    averaged over one more such window; in 3-D the field criterion of Sec. 3
+    over 2000 steps.  Returns the reductions, centre values and fields."""
     import numpy as np
     from paper_2509_01099_gb300 import analysis as A
     from synthetic import temperature_noise
@@ -843,6 +847,21 @@ def steady_run(pkg, torch, dim, n, Ra, init, tol, max_steps):
         steps, st = r["steps"], r["status"]
     wall = time.perf_counter() - t0
     red = s.reduce(check=False)
+    red_inst = dict(red)
+    if dim == 2:
+        # the integral quantities as means over one more window (100 samples
+        # 1000 steps apart): at Ra = 1e8 a small residual oscillation survives
+        # the window criterion, and a single sample of <Nu> or Nu_middle can
+        # sit on its crest
+        keys = ("Nu", "Nu_hot", "Nu_cold", "Nu_middle", "Re", "Re_uv")
+        acc = {k: 0.0 for k in keys}
+        for _ in range(100):
+            b.step(1000)
+            r = s.reduce(check=False)
+            for k in keys:
+                acc[k] += r[k] / 100
+        red.update(acc)
+        steps += 100_000
     f = s.fields()
     uf = s.info.u_f
     fields = {k: np.asarray(v) for k, v in f.items()}
@@ -855,7 +874,8 @@ def steady_run(pkg, torch, dim, n, Ra, init, tol, max_steps):
            "Nu": red["Nu"], "Nu_hot": red["Nu_hot"], "Nu_cold": red["Nu_cold"],
            "Nu_middle": red["Nu_middle"] if dim == 2 else None, "Re": red["Re"],
            "Re_uv": red["Re_uv"], "T_c": c["T"], "u_c": c["u"], "v_c": c["v"],
-           "omega_c": abs(c["omega"])}
+           "omega_c": abs(c["omega"]),
+           "Nu_at_criterion": red_inst["Nu"], "Nu_middle_at_criterion": red_inst["Nu_middle"]}
     if b is not None:
         b.close()
     else:
@@ -959,6 +979,55 @@ def flush_l2(flush):
     flush[1].sum()
 
 
+def cnn_gemm(pkg, torch, batch=16, reps=20):
+    """Device time of the warm-start network's products at batch 16: for every
+    convolution of the decoder (16^2 .. 256^2) the forward product (im2col rows
+    x weights), the data gradient (dY x W^T) and the weight gradient
+    (im2col^T x dY), on path 1 (mma.sync) and path 2 (tcgen05 + TMA, where
+    its 16-byte conditions hold), with 3 warm-up calls and `reps` timed ones.
+    Algorithmic bytes: the BF16 operands read once and the FP32 result
+    written once."""
+    import ctypes
+    from paper_2509_01099_gb300.islbm import load_library
+    lib = load_library()
+    st = torch.cuda.current_stream()
+    S = ctypes.c_void_p(st.cuda_stream)
+    layers = [(16, 64, 64), (32, 64, 48), (64, 48, 32), (128, 32, 16), (256, 16, 16), (256, 16, 3)]
+    g = torch.Generator(device="cuda").manual_seed(0)
+    for hw, cin, cout in layers:
+        M, kp = batch * hw * hw, (9 * cin + 15) // 16 * 16
+        for name, m, n, k, ta, tb in ((f"fwd {hw}^2 {cin}->{cout}", M, cout, kp, 0, 0),
+                                      (f"dgrad {hw}^2", M, kp, cout, 0, 1),
+                                      (f"wgrad {hw}^2", kp, cout, M, 1, 0)):
+            A = torch.randn((k, m) if ta else (m, k), device="cuda", generator=g).to(torch.bfloat16)
+            B = torch.randn((n, k) if tb else (k, n), device="cuda", generator=g).to(torch.bfloat16)
+            C = torch.zeros((m, n), device="cuda")
+            row = {"cnn_gemm": name, "M": m, "N": n, "K": k}
+            for path in (1, 2):
+                if path == 2 and (A.shape[1] % 8 or B.shape[1] % 8):
+                    continue
+                call = lambda: lib.islbm_cnn_gemm_bf16_ex(
+                    ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                    ctypes.c_void_p(C.data_ptr()), None, m, n, k, A.shape[1], B.shape[1], n, ta,
+                    tb, 0, path, S)
+                for _ in range(3):
+                    if call() != 0:
+                        raise RuntimeError(f"islbm_cnn_gemm_bf16_ex failed on {name}")
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(st)
+                for _ in range(reps):
+                    call()
+                e1.record(st)
+                torch.cuda.synchronize()
+                us = e0.elapsed_time(e1) * 1e3 / reps
+                tag = "tcgen05" if path == 2 else "mma_sync"
+                row[f"us_{tag}"] = round(us, 2)
+                row[f"tflops_{tag}"] = round(2.0 * m * n * k / us / 1e6, 2)
+                row[f"gbps_{tag}"] = round((2 * (m * k + k * n) + 4 * m * n) / us / 1e3, 1)
+            print(json.dumps(row), flush=True)
+
+
 def timed_steps(pkg, solver, steps, warmup, flush, torch):
     """Device time of `steps` single-step launches, each after an L2 flush."""
     from synthetic import temperature_noise
@@ -1005,6 +1074,9 @@ def main():
              torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")]
     if args.sweep:
         sweep(args, pkg, torch, flush)
+        return
+    if args.cnn_gemm:
+        cnn_gemm(pkg, torch)
         return
     if args.steady:
         steady(args, pkg, torch)

@@ -373,7 +373,8 @@ ISLBM_API islbm_status islbm_batch_run_to_steady_nu(islbm_batch_t b, double tol,
  * accumulate != 0 adds to C.  A, B: bf16; C, bias: FP32 (bias may be NULL).
  * Path: when lda and ldb are multiples of 8 and A, B are 16-byte aligned, the
  * fifth-generation tensor cores (tcgen05.mma, accumulator in tensor memory;
- * 128 x N tiles, 64-wide k stages); else the warp-level mma.sync kernel.
+ * 128 x 16 / 32 / 64 tiles, operands copied by TMA in 64-wide k stages),
+ * except when K <= 32; else the warp-level mma.sync kernel.
  * When the output tiles are too few to fill the GPU the K range is split and
  * the splits' partial tiles are added in a fixed order, so results do not
  * depend on scheduling.  The partial tiles live in one split-K workspace per

@@ -380,7 +380,10 @@ extern "C" islbm_status islbm_cnn_gemm_bf16_ex(const void* A, const void* B, flo
     return ISLBM_ERR_ARG;
   const bool tc_ok = islbm::cnn_gemm_tc_supported(A, B, M, N, K, lda, ldb);
   if (path == 2 && !tc_ok) return ISLBM_ERR_ARG;
-  if (path == 1 || !tc_ok)
+  // path 0: the tensor-core kernel, except for products with K <= 32 (the
+  // data gradients of the narrow layers): a 128 x 64 tile then does too little
+  // work for its setup, and the mma.sync kernel is faster (measured on GB300)
+  if (path == 1 || !tc_ok || (path == 0 && K <= 32))
     return gemm_mma_sync(A, B, C, bias, M, N, K, lda, ldb, ldc, transA, transB, accumulate,
                          stream);
   return launched(islbm::launch_cnn_gemm_tc(A, B, C, bias, M, N, K, lda, ldb, ldc, transA, transB,

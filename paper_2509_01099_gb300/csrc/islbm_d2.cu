@@ -14,6 +14,7 @@
 // stored after the collision instead of before it.
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -121,10 +122,11 @@ struct NodeIO<Neq16> {
 // The buoyancy F = rho g beta (T - T_ref) acts along +y; u = (sum e f + F/2)/rho.
 // The populations carry T - T_s, which is also the temperature of the
 // equilibrium fluxes u T and of a_T T.
-// Returns rho, u and T of the pre-collision state.
+// Returns rho, u and T of the pre-collision state, and in m_o the moments of
+// the post-collision state: drho, jx, jy + F_y, T - T_s.
 template <typename L, typename R>
-__device__ __forceinline__ void collide(L (&f)[9], L (&g)[5], const P2<R>& p, L& rho_o,
-                                        L& ux_o, L& uy_o, L& T_o) {
+__device__ __forceinline__ void collide_m(L (&f)[9], L (&g)[5], const P2<R>& p, L& rho_o,
+                                          L& ux_o, L& uy_o, L& T_o, L (&m_o)[4]) {
   using K = Lanes<L>;
   auto c = [](double v) { return K::bc((typename K::S)v); };
   // pre-collision moments
@@ -206,6 +208,17 @@ __device__ __forceinline__ void collide(L (&f)[9], L (&g)[5], const P2<R>& p, L&
   ux_o = ux;
   uy_o = uy;
   T_o = Tr;
+  m_o[0] = drho;
+  m_o[1] = jx;
+  m_o[2] = ladd(jy, Fy);
+  m_o[3] = Tr;
+}
+
+template <typename L, typename R>
+__device__ __forceinline__ void collide(L (&f)[9], L (&g)[5], const P2<R>& p, L& rho_o,
+                                        L& ux_o, L& uy_o, L& T_o) {
+  L m[4];
+  collide_m(f, g, p, rho_o, ux_o, uy_o, T_o, m);
 }
 
 // Interpolated pull of one population (Sec. 2.2): the value at node (x, y) is
@@ -790,22 +803,27 @@ __device__ __forceinline__ void tile_body(const S* __restrict__ sm, const float4
     for (int i = 0; i < 9; ++i) fn[i] = make_float2(f[i][m], f[i][m + 1]);
 #pragma unroll
     for (int i = 0; i < 5; ++i) gn[i] = make_float2(g[i][m], g[i][m + 1]);
-    float2 rho, ux, uy, T;
-    collide(fn, gn, p, rho, ux, uy, T);
+    float2 rho, ux, uy, T, mm[4];
+    collide_m(fn, gn, p, rho, ux, uy, T, mm);
     const size_t idx = (size_t)y * p.pitch + x;
     if constexpr (is_neq<O>::value) {
-      float a[9], b[5];
+      // rows y (low halves) and y + 1 (high halves) encoded together
+      float t0, ti;
+      trest(p.a_T, t0, ti);
+      unsigned rr[14];
+      neq_remainders2x2(fn, gn, mm, t0, ti, rr);
+      unsigned short* h = reinterpret_cast<unsigned short*>(fout);
+      float* mo = neq_moments(fout, p.plane);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) a[i] = fn[i].x;
+      for (int i = 0; i < 14; ++i) h[(size_t)i * p.plane + idx] = (unsigned short)(rr[i] & 0xFFFFu);
 #pragma unroll
-      for (int i = 0; i < 5; ++i) b[i] = gn[i].x;
-      NodeIO<Neq16>::store(fout, idx, p.plane, p.a_T, a, b);
+      for (int k = 0; k < 4; ++k) mo[(size_t)k * p.plane + idx] = mm[k].x;
       if (y + 1 < p.y1) {
+        const size_t idx1 = idx + p.pitch;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) a[i] = fn[i].y;
+        for (int i = 0; i < 14; ++i) h[(size_t)i * p.plane + idx1] = (unsigned short)(rr[i] >> 16);
 #pragma unroll
-        for (int i = 0; i < 5; ++i) b[i] = gn[i].y;
-        NodeIO<Neq16>::store(fout, idx + p.pitch, p.plane, p.a_T, a, b);
+        for (int k = 0; k < 4; ++k) mo[(size_t)k * p.plane + idx1] = mm[k].y;
       }
     } else {
       unsigned r = sr_seed(idx, p.step);
@@ -896,81 +914,74 @@ struct TmaStage {
   static constexpr unsigned LOADED = PLANES;           // bytes the copies bring
   static constexpr unsigned TABLES = (unsigned)((2 * kTX + 2 * TileGeom<S, R>::TY) * 16);
   static constexpr unsigned BYTES = PLANES + TABLES;
+  static constexpr unsigned EXTRA = 0;                 // shared memory behind the ring
   static_assert(PLANES % 128 == 0 && BYTES % 128 == 0, "stages keep the TMA's 128-byte alignment");
 };
 
 // Non-equilibrium storage: the copies bring the FP16 remainders (box of
 // kTX + 16 columns from x0 - 8, one 16-byte chunk of halo each side) and the
-// FP32 moments (kTX + 8 columns from x0 - 4); the decode then overwrites the
-// stage with the FP32 deviations in the layout of TileGeom<float, R>, which is
-// what tile_body reads.
+// FP32 moments (kTX + 8 columns from x0 - 4) into the stage; the decode writes
+// the FP32 deviations, in the layout of TileGeom<float, R> that tile_body
+// reads, into one buffer of DECODED bytes behind the ring (EXTRA).
 template <int R>
 struct TmaStage<Neq16, R> {
   using Staged = float;
   using G = TileGeom<float, R>;
   static constexpr int HW = kTX + 16;                  // remainder row width (halves)
   static constexpr unsigned RAW_H = (unsigned)(14 * G::SH * HW * 2);
+  static constexpr unsigned M_OFF = (RAW_H + 127u) / 128u * 128u;
   static constexpr unsigned RAW_M = (unsigned)(4 * G::SH * G::SW * 4);
   static constexpr unsigned LOADED = RAW_H + RAW_M;
-  static constexpr unsigned DECODED = (unsigned)(14 * G::PLANE * 4);
-  static constexpr unsigned PLANES = ((LOADED > DECODED ? LOADED : DECODED) + 127u) / 128u * 128u;
+  static constexpr unsigned PLANES = (M_OFF + RAW_M + 127u) / 128u * 128u;
   static constexpr unsigned TABLES = (unsigned)((2 * kTX + 2 * G::TY) * 16);
   static constexpr unsigned BYTES = PLANES + TABLES;
-  static_assert(RAW_H % 128 == 0 && BYTES % 128 == 0, "stages keep the TMA's 128-byte alignment");
+  static constexpr unsigned DECODED = (unsigned)(14 * G::PLANE * 4);
+  static constexpr unsigned EXTRA = (DECODED + 127u) / 128u * 128u;
+  static_assert(BYTES % 128 == 0 && M_OFF % 128 == 0, "TMA destinations stay 128-byte aligned");
   static_assert(G::SW == kTX + 8, "the moment box covers the decoded window");
 };
 
-// Decode of a staged Neq16 tile in place (see TmaStage<Neq16, R>): every
-// thread first reads the remainders and moments of its nodes into registers,
-// then, after a CTA-wide barrier, writes their FP32 deviations over the stage.
-// Ends with a barrier.  Nodes outside the mesh were zero-filled by the copy and
-// decode to zero deviations, as the FP32 stage holds there.
+// Decode of a staged Neq16 tile into the FP32 buffer `out` (see
+// TmaStage<Neq16, R>), two neighbouring columns per thread and pass.  The
+// caller's next CTA-wide barrier publishes the buffer.  Nodes outside the mesh
+// were zero-filled by the copy and decode to zero deviations, as the FP32
+// stage holds there.
 template <int R>
-__device__ __forceinline__ void neq_decode_tile(unsigned char* stage, float aT) {
+__device__ __forceinline__ void neq_decode_tile(const unsigned char* stage, float* out_f,
+                                                float aT) {
   using ST = TmaStage<Neq16, R>;
   using G = typename ST::G;
   constexpr int NODES = G::PLANE, SW = G::SW, HW = ST::HW;
-  constexpr int PER = (NODES + kThreads - 1) / kThreads;
-  static_assert(PER <= 3, "registers hold at most three nodes per thread");
-  const unsigned short* rh = reinterpret_cast<const unsigned short*>(stage);
-  const float* rm = reinterpret_cast<const float*>(stage + ST::RAW_H);
-  unsigned short r[PER][14];
-  float m[PER][4];
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int n = threadIdx.x + k * kThreads;
-    if (n < NODES) {
-      const int row = n / SW, c = n - row * SW;
-#pragma unroll
-      for (int i = 0; i < 14; ++i) r[k][i] = rh[(i * G::SH + row) * HW + c + 4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) m[k][j] = rm[j * NODES + n];
-    }
-  }
-  __syncthreads();
+  constexpr int PAIRS = NODES / 2;
+  static_assert(SW % 2 == 0 && HW % 2 == 0, "node pairs share one 32-bit word");
+  const unsigned* rh = reinterpret_cast<const unsigned*>(stage);
+  const float2* rm = reinterpret_cast<const float2*>(stage + ST::M_OFF);
+  float2* out = reinterpret_cast<float2*>(out_f);
   float t0, ti;
   trest(aT, t0, ti);
-  float* out = reinterpret_cast<float*>(stage);
+  for (int q = threadIdx.x; q < PAIRS; q += kThreads) {   // nodes 2q, 2q + 1 of the window
+    const int n = 2 * q;
+    const int row = n / SW, c = n - row * SW;
+    unsigned r[14];
 #pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int n = threadIdx.x + k * kThreads;
-    if (n < NODES) {
-      float f[9], g[5];
-      neq_decode2(m[k][0], m[k][1], m[k][2], m[k][3], r[k], t0, ti, f, g);
+    for (int i = 0; i < 14; ++i) r[i] = rh[((i * G::SH + row) * HW + c + 4) / 2];
+    float2 f[9], g[5];
+    neq_decode2x2(rm[q], rm[(NODES + n) / 2], rm[(2 * NODES + n) / 2], rm[(3 * NODES + n) / 2],
+                  r, t0, ti, f, g);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) out[i * NODES + n] = f[i];
+    for (int i = 0; i < 9; ++i) out[(i * NODES + n) / 2] = f[i];
 #pragma unroll
-      for (int i = 0; i < 5; ++i) out[(9 + i) * NODES + n] = g[i];
-    }
+    for (int i = 0; i < 5; ++i) out[((9 + i) * NODES + n) / 2] = g[i];
   }
-  __syncthreads();
 }
 
 // CTAs per SM that the shared memory of a k_step_tma instantiation allows (two
 // when its ring fits in half of the 228 KB); the register budget follows.
 template <typename S, int R, int STAGES>
 constexpr int tma_ctas_per_sm() {
-  return (size_t)STAGES * TmaStage<S, R>::BYTES + 2048 <= 114 * 1024 ? 2 : 1;
+  return (size_t)STAGES * TmaStage<S, R>::BYTES + TmaStage<S, R>::EXTRA + 1536 <= 114 * 1024
+             ? 2
+             : 1;
 }
 
 // tmap_m: the moment planes of a Neq16 buffer (unused for the other forms).
@@ -984,7 +995,9 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
   using G = TileGeom<SS, R>;
   constexpr int TY = G::TY, HX = G::HX;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)STAGES * ST::BYTES);
+  float* dec = reinterpret_cast<float*>(smem_raw + (size_t)STAGES * ST::BYTES);   // Neq16
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(smem_raw + (size_t)STAGES * ST::BYTES + ST::EXTRA);
   __shared__ int tile_of[STAGES];   // claimed tile of each stage (dynamic order)
   const int ntx = (p.nx + kTX - 1) / kTX, nty = (p.y1 - p.y0 + TY - 1) / TY;
   const int ntiles = ntx * nty;
@@ -1009,7 +1022,7 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
     mbar_expect_tx(&bars[st], ST::LOADED + 2 * (xb + yb));
     if constexpr (is_neq<S>::value) {
       tma_load_3d(dst, &tmap, x0 - 8, ry0, 0, &bars[st]);
-      tma_load_3d(dst + ST::RAW_H, &tmap_m, x0 - HX, ry0, 0, &bars[st]);
+      tma_load_3d(dst + ST::M_OFF, &tmap_m, x0 - HX, ry0, 0, &bars[st]);
     } else {
       tma_load_3d(dst, &tmap, x0 - HX, ry0, 0, &bars[st]);
     }
@@ -1046,6 +1059,9 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
     int next = t + stride;
     if (dynamic && threadIdx.x == 0) next = stride + atomicAdd(&sched[1], 1);
     const bool ok = mbar_wait(&bars[st], (unsigned)(k / STAGES) & 1u);
+    // FP16NEQ: decode before the barrier, which then also publishes the decoded
+    // tile (a thread whose wait gave up decodes stale data that is never used)
+    if constexpr (is_neq<S>::value) neq_decode_tile<R>(smem_raw + (size_t)st * ST::BYTES, dec, p.a_T);
     if (__syncthreads_or(!ok)) {
       // a copy did not arrive: flag it, drain what is still in flight, leave
       if (threadIdx.x == 0) {
@@ -1059,8 +1075,8 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
     }
     int x0, y0, ry0;
     tile_origin(t, x0, y0, ry0);
-    if constexpr (is_neq<S>::value) neq_decode_tile<R>(smem_raw + (size_t)st * ST::BYTES, p.a_T);
     const SS* sm = reinterpret_cast<const SS*>(smem_raw + (size_t)st * ST::BYTES);
+    if constexpr (is_neq<S>::value) sm = dec;
     const float4* tab = tables(st);
     tile_body<SS, R, false, S>(sm, tab, tab + kTX, tab + 2 * kTX, tab + 2 * kTX + TY, x0, y0,
                                ry0, fout, p);
@@ -1097,8 +1113,10 @@ struct alignas(128) BatchCav {
   S* out[2];               // output buffer when reading buffer 0 / 1
 };
 
+// Two CTAs per SM fit the shared memory of every 8-row form (FP16NEQ's
+// decoded tile included); the register budget is held to that.
 template <typename S, int R, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, (R == 2 ? 2 : 1))
     k_step_tma_batch(const BatchCav<S>* __restrict__ cavs, const int2* __restrict__ items,
                      int nitems, int parity, unsigned step, int* err) {
   using ST = TmaStage<S, R>;
@@ -1107,7 +1125,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int TY = G::TY, HX = G::HX;
   constexpr unsigned BUF = ST::PLANES;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)STAGES * BUF);
+  float* dec = reinterpret_cast<float*>(smem_raw + (size_t)STAGES * BUF);   // Neq16
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)STAGES * BUF + ST::EXTRA);
   auto origin = [&](const P2<float>& p, int t, int& x0, int& y0, int& ry0) {
     const int ntx = (p.nx + kTX - 1) / kTX;
     const int ty = t / ntx;
@@ -1124,7 +1143,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_expect_tx(&bars[st], ST::LOADED);
     if constexpr (is_neq<S>::value) {
       tma_load_3d(dst, &cv.map[parity], x0 - 8, ry0, 0, &bars[st]);
-      tma_load_3d(dst + ST::RAW_H, &cv.mapm[parity], x0 - HX, ry0, 0, &bars[st]);
+      tma_load_3d(dst + ST::M_OFF, &cv.mapm[parity], x0 - HX, ry0, 0, &bars[st]);
     } else {
       tma_load_3d(dst, &cv.map[parity], x0 - HX, ry0, 0, &bars[st]);
     }
@@ -1144,6 +1163,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (i >= nitems) break;
     const int st = k % STAGES;
     const bool ok = mbar_wait(&bars[st], (unsigned)(k / STAGES) & 1u);
+    const int2 it = items[i];
+    const BatchCav<S>& cv = cavs[it.x];
+    // FP16NEQ: decode before the barrier, which then also publishes the decoded tile
+    if constexpr (is_neq<S>::value) neq_decode_tile<R>(smem_raw + (size_t)st * BUF, dec, cv.p.a_T);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicExch(err, 1);
@@ -1155,14 +1178,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       return;
     }
-    const int2 it = items[i];
-    const BatchCav<S>& cv = cavs[it.x];
     P2<float> p = cv.p;
     p.step = step;
     int x0, y0, ry0;
     origin(p, it.y, x0, y0, ry0);
-    if constexpr (is_neq<S>::value) neq_decode_tile<R>(smem_raw + (size_t)st * BUF, p.a_T);
     const SS* sm = reinterpret_cast<const SS*>(smem_raw + (size_t)st * BUF);
+    if constexpr (is_neq<S>::value) sm = dec;
     tile_body<SS, R, false, S>(sm, p.px[0] + x0, p.px[1] + x0, p.py[0] + y0, p.py[1] + y0, x0,
                                y0, ry0, cv.out[parity], p);
     __syncthreads();
@@ -1198,10 +1219,23 @@ cudaError_t launch_tiled(const Solver& s, const S* in, S* out, const P2<float>& 
 // stride is up to 4% faster, beyond ~50 the claimed order wins (1.47x at 8192^2).
 constexpr int kDynamicTilesPerCta = 24;
 
+// Tuning override of that choice: ISLBM_TMA_SCHEDULE=fixed / claimed (unset:
+// automatic).
+int tma_schedule_override() {
+  static const int v = [] {
+    const char* e = std::getenv("ISLBM_TMA_SCHEDULE");
+    if (!e) return -1;
+    if (std::strcmp(e, "fixed") == 0) return 0;
+    if (std::strcmp(e, "claimed") == 0) return 1;
+    return -1;
+  }();
+  return v;
+}
+
 template <typename S, int R, int STAGES>
 cudaError_t launch_tma(const Solver& s, int cur, S* out, const P2<float>& p) {
   using G = TileGeom<typename TmaStage<S, R>::Staged, R>;
-  constexpr size_t smem = (size_t)STAGES * TmaStage<S, R>::BYTES + 64;
+  constexpr size_t smem = (size_t)STAGES * TmaStage<S, R>::BYTES + TmaStage<S, R>::EXTRA + 64;
   int blocks_per_sm = 0;
   const cudaError_t e = launch_setup_once(
       reinterpret_cast<const void*>(k_step_tma<S, R, STAGES>),
@@ -1218,7 +1252,8 @@ cudaError_t launch_tma(const Solver& s, int cur, S* out, const P2<float>& p) {
   const int ntiles = ((s.n[0] + kTX - 1) / kTX) * ((step_rows(s) + G::TY - 1) / G::TY);
   const int grid = std::min(ntiles, s.sm_count * blocks_per_sm);
   // claimed tiles pay off once a CTA walks more than a few dozen tiles
-  const int dynamic = ntiles >= kDynamicTilesPerCta * grid ? 1 : 0;
+  const int ov = tma_schedule_override();
+  const int dynamic = ov >= 0 ? ov : (ntiles >= kDynamicTilesPerCta * grid ? 1 : 0);
   k_step_tma<S, R, STAGES><<<grid, kThreads, smem, s.stream>>>(
       *reinterpret_cast<const CUtensorMap*>(s.tmap[cur]),
       *reinterpret_cast<const CUtensorMap*>(s.tmap_m[cur]), out, p, s.derr, dynamic);
@@ -1420,7 +1455,7 @@ cudaError_t make_group_impl(const std::vector<Solver*>& members, int sm_count,
                             cudaStream_t stream, BatchGroup** out) {
   using G = TileGeom<typename TmaStage<S, R>::Staged, R>;
   auto* g = new BatchGroupImpl<S, R>();
-  g->smem = (size_t)2 * TmaStage<S, R>::PLANES + 64;
+  g->smem = (size_t)2 * TmaStage<S, R>::PLANES + TmaStage<S, R>::EXTRA + 64;
   cudaError_t e = cudaFuncSetAttribute(k_step_tma_batch<S, R, 2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem);
   int bps = 0;
