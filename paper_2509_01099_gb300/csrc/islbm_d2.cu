@@ -1037,10 +1037,10 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
   auto tile_at = [&](int k) {
     return (k < STAGES || !dynamic) ? (int)blockIdx.x + k * (int)gridDim.x : tile_of[k % STAGES];
   };
+  if constexpr (is_neq<S>::value) {
   if (threadIdx.x == 0) {
     asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tmap) : "memory");
-    if constexpr (is_neq<S>::value)
-      asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tmap_m) : "memory");
+    asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tmap_m) : "memory");
     for (int st = 0; st < STAGES; ++st) mbar_init(&bars[st], 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -1088,6 +1088,96 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
         issue(next, st);
       }
     }
+  }
+  } else {
+    // FP32 and 16-bit storage: a "full" and an "empty" mbarrier per stage and
+    // no CTA-wide barrier in the loop.  Every warp waits for a stage's copies
+    // itself, computes its part of the tile and arrives on the stage's empty
+    // barrier; thread 0 refills the stage once all warps have arrived.  Warps
+    // run up to STAGES - 1 tiles apart instead of meeting twice per tile.
+    // In the claimed order a stage's tile index is written by thread 0 before
+    // the arrival that completes the stage's phase, so a warp reads it after
+    // its wait; with no tile left the phase is completed by a plain arrival.
+    // A wait that fails raises the CTA's abort flag (every other wait then
+    // gives up at once) and the error flag; thread 0 drains the stages it
+    // filled before it leaves.
+    uint64_t* full = bars;
+    uint64_t* empty = bars + STAGES;
+    volatile int* abort = reinterpret_cast<volatile int*>(bars + 2 * STAGES);
+    if (threadIdx.x == 0) {
+      asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tmap) : "memory");
+      for (int st = 0; st < STAGES; ++st) {
+        mbar_init(&full[st], 1);
+        mbar_init(&empty[st], kThreads / 32);
+      }
+      *abort = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    int filled = 0;   // thread 0: stage uses filled so far (copies or a plain arrival)
+    int seen = 0;     // thread 0: stage uses whose phase it has seen complete
+    if (threadIdx.x == 0)
+      for (int st = 0; st < STAGES; ++st) {
+        const int t = blockIdx.x + st * gridDim.x;
+        if (t < ntiles) {
+          issue(t, st);
+          filled = st + 1;
+        }
+      }
+    const unsigned lane = threadIdx.x & 31u;
+    auto fail = [&]() {
+      if (!*abort) atomicExch(&sched[0], 1);
+      *abort = 1;
+    };
+    for (int k = 0;; ++k) {
+      const int st = k % STAGES;
+      const unsigned ph = (unsigned)(k / STAGES) & 1u;
+      const bool fixed = k < STAGES || !dynamic;
+      int t = (int)blockIdx.x + k * (int)gridDim.x;
+      if (fixed && t >= ntiles) break;
+      if (!__all_sync(0xffffffffu, mbar_wait_or_abort(&full[st], ph, abort))) {
+        if (lane == 0) fail();
+        break;
+      }
+      if (threadIdx.x == 0) seen = k + 1;
+      if (!fixed) {
+        t = tile_of[st];
+        if (t >= ntiles) break;
+      }
+      // the tile of this stage's next use; a claim is made now so that its
+      // latency overlaps the compute
+      int next = t + stride;
+      if (dynamic && threadIdx.x == 0) next = stride + atomicAdd(&sched[1], 1);
+      int x0, y0, ry0;
+      tile_origin(t, x0, y0, ry0);
+      const float4* tab = tables(st);
+      tile_body<SS, R, false, S>(reinterpret_cast<const SS*>(smem_raw + (size_t)st * ST::BYTES),
+                                 tab, tab + kTX, tab + 2 * kTX, tab + 2 * kTX + TY, x0, y0, ry0,
+                                 fout, p);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+      int pfail = 0;
+      if (threadIdx.x == 0 && (next < ntiles || dynamic)) {
+        // refill stage st for use k + STAGES once every warp is done with use k
+        if (!mbar_wait_or_abort(&empty[st], ph, abort)) {
+          fail();
+          pfail = 1;
+        } else {
+          if (dynamic) tile_of[st] = next;
+          if (next < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            issue(next, st);
+          } else {
+            mbar_arrive(&full[st]);   // no tile left: complete the phase with no bytes
+          }
+          filled = k + STAGES + 1;
+        }
+      }
+      if (__shfl_sync(0xffffffffu, pfail, 0)) break;
+    }
+    // copies still in flight land before the CTA's shared memory is released
+    if (threadIdx.x == 0)
+      for (int u = seen; u < filled; ++u) mbar_wait(&full[u % STAGES], (unsigned)(u / STAGES) & 1u);
   }
   if (dynamic && threadIdx.x == 0) {
     // every claim of this CTA is done; the last CTA out resets the counters
@@ -1148,6 +1238,7 @@ __global__ void __launch_bounds__(kThreads, (R == 2 ? 2 : 1))
       tma_load_3d(dst, &cv.map[parity], x0 - HX, ry0, 0, &bars[st]);
     }
   };
+  if constexpr (is_neq<S>::value) {
   if (threadIdx.x == 0) {
     for (int st = 0; st < STAGES; ++st) mbar_init(&bars[st], 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -1194,6 +1285,74 @@ __global__ void __launch_bounds__(kThreads, (R == 2 ? 2 : 1))
         issue(in, st);
       }
     }
+  }
+  } else {
+    // FP32 and 16-bit storage: full / empty mbarriers per stage and no
+    // CTA-wide barrier in the loop, as in k_step_tma.
+    uint64_t* full = bars;
+    uint64_t* empty = bars + STAGES;
+    volatile int* abort = reinterpret_cast<volatile int*>(bars + 2 * STAGES);
+    if (threadIdx.x == 0) {
+      for (int st = 0; st < STAGES; ++st) {
+        mbar_init(&full[st], 1);
+        mbar_init(&empty[st], kThreads / 32);
+      }
+      *abort = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    int filled = 0, seen = 0;   // thread 0: stage uses filled / seen complete
+    if (threadIdx.x == 0)
+      for (int st = 0; st < STAGES; ++st) {
+        const int i = blockIdx.x + st * gridDim.x;
+        if (i < nitems) {
+          issue(i, st);
+          filled = st + 1;
+        }
+      }
+    const unsigned lane = threadIdx.x & 31u;
+    auto fail = [&]() {
+      if (!*abort) atomicExch(err, 1);
+      *abort = 1;
+    };
+    for (int k = 0;; ++k) {
+      const int i = blockIdx.x + k * gridDim.x;
+      if (i >= nitems) break;
+      const int st = k % STAGES;
+      const unsigned ph = (unsigned)(k / STAGES) & 1u;
+      if (!__all_sync(0xffffffffu, mbar_wait_or_abort(&full[st], ph, abort))) {
+        if (lane == 0) fail();
+        break;
+      }
+      if (threadIdx.x == 0) seen = k + 1;
+      const int2 it = items[i];
+      const BatchCav<S>& cv = cavs[it.x];
+      P2<float> p = cv.p;
+      p.step = step;
+      int x0, y0, ry0;
+      origin(p, it.y, x0, y0, ry0);
+      tile_body<SS, R, false, S>(reinterpret_cast<const SS*>(smem_raw + (size_t)st * BUF),
+                                 p.px[0] + x0, p.px[1] + x0, p.py[0] + y0, p.py[1] + y0, x0, y0,
+                                 ry0, cv.out[parity], p);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+      int pfail = 0;
+      const int in = i + STAGES * gridDim.x;
+      if (threadIdx.x == 0 && in < nitems) {
+        // refill stage st once every warp is done with it
+        if (!mbar_wait_or_abort(&empty[st], ph, abort)) {
+          fail();
+          pfail = 1;
+        } else {
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          issue(in, st);
+          filled = k + STAGES + 1;
+        }
+      }
+      if (__shfl_sync(0xffffffffu, pfail, 0)) break;
+    }
+    if (threadIdx.x == 0)
+      for (int u = seen; u < filled; ++u) mbar_wait(&full[u % STAGES], (unsigned)(u / STAGES) & 1u);
   }
 }
 

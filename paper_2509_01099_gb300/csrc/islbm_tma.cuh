@@ -67,6 +67,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned phase) {
   return false;
 }
 
+// Bounded wait that also gives up as soon as `abort` (a CTA-wide flag in
+// shared memory, raised by a thread whose own wait failed) is set.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, unsigned phase,
+                                                   const volatile int* abort) {
+  if (mbar_try_wait(bar, phase)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < kWaitMaxPolls; ++i) {
+    if (mbar_try_wait(bar, phase)) return true;
+    if ((i & 63) == 63 && (*abort || global_ns() - t0 > kWaitLimitNs)) return false;
+  }
+  return false;
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
                                             uint64_t* bar) {
   asm volatile(
