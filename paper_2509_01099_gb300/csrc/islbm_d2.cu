@@ -13,6 +13,7 @@
 // which is the paper's collide -> stream -> interpolate cycle with the state
 // stored after the collision instead of before it.
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -636,6 +637,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 
+constexpr int kFixedOrder = INT_MAX;   // k0 of k_step_tma: no tile is claimed
 constexpr int kTX = 64;       // tile width
 constexpr int kRG = 4;        // row groups per tile
 constexpr int kThreads = kTX * kRG;
@@ -889,13 +891,17 @@ __global__ void __launch_bounds__(kThreads, 2)
 // tiles are in flight while the current tile is computed and the compute
 // reads nothing but shared memory.
 //
-// Tile order.  The first STAGES tiles of a CTA are blockIdx.x + k * gridDim.x.
-// With `dynamic` = 0 every later one follows the same stride.  With `dynamic`
-// = 1 each later tile is claimed from a device counter one tile ahead of its
-// use, so SMs that run ahead take more tiles and the tiles in flight stay a
-// compact band of rows (on large meshes, where a CTA walks hundreds of tiles,
-// the fixed stride lets the CTAs drift apart).  The last CTA to finish resets
-// the counter.  A tile index at or beyond the tile count ends the CTA's walk.
+// Tile order.  The tile of a CTA's k-th stage use is blockIdx.x + k * gridDim.x
+// for k < k0 (k0 >= STAGES, and k0 * gridDim.x <= the tile count, so these
+// tiles all exist).  From use k0 on, each tile is claimed from a device counter
+// STAGES uses ahead of its use (tiles k0 * gridDim.x and up), so SMs that run
+// ahead take more tiles: with k0 = STAGES on large meshes, where a CTA walks
+// hundreds of tiles, the claimed order keeps the tiles in flight a compact band
+// of rows (the fixed stride lets the CTAs drift apart); with k0 a tile or two
+// short of the CTA's share on small meshes, only the last tiles are claimed and
+// even out the SMs' finishing times.  k0 = INT_MAX: the fixed stride
+// throughout.  The last CTA to finish resets the counter.  A tile index at or
+// beyond the tile count ends the CTA's walk.
 //
 // Every mbarrier wait is bounded: on timeout the CTA records an error flag,
 // drains its outstanding copies (again bounded) and leaves through the same
@@ -988,7 +994,7 @@ constexpr int tma_ctas_per_sm() {
 template <typename S, int R, int STAGES>
 __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
     k_step_tma(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_m,
-               S* __restrict__ fout, P2<float> p, int* sched, int dynamic) {
+               S* __restrict__ fout, P2<float> p, int* sched, int k0) {
   static_assert(STAGES >= 2, "a claimed tile is published by the barriers of the next use");
   using ST = TmaStage<S, R>;
   using SS = typename ST::Staged;
@@ -998,7 +1004,7 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
   float* dec = reinterpret_cast<float*>(smem_raw + (size_t)STAGES * ST::BYTES);   // Neq16
   uint64_t* bars =
       reinterpret_cast<uint64_t*>(smem_raw + (size_t)STAGES * ST::BYTES + ST::EXTRA);
-  __shared__ int tile_of[STAGES];   // claimed tile of each stage (dynamic order)
+  __shared__ int tile_of[STAGES];   // claimed tile of each stage (uses from k0 on)
   const int ntx = (p.nx + kTX - 1) / kTX, nty = (p.y1 - p.y0 + TY - 1) / TY;
   const int ntiles = ntx * nty;
   const int stride = STAGES * (int)gridDim.x;
@@ -1035,7 +1041,7 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
   // after the CTA-wide barrier that ends use k - STAGES; the barriers of use
   // k - STAGES + 1 (STAGES >= 2) publish it to the other threads.
   auto tile_at = [&](int k) {
-    return (k < STAGES || !dynamic) ? (int)blockIdx.x + k * (int)gridDim.x : tile_of[k % STAGES];
+    return k < k0 ? (int)blockIdx.x + k * (int)gridDim.x : tile_of[k % STAGES];
   };
   if constexpr (is_neq<S>::value) {
   if (threadIdx.x == 0) {
@@ -1057,7 +1063,7 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
     // the tile for this stage's next use; a claim is made now so that its
     // latency overlaps the compute (the value is needed when the stage frees up)
     int next = t + stride;
-    if (dynamic && threadIdx.x == 0) next = stride + atomicAdd(&sched[1], 1);
+    if (k + STAGES >= k0 && threadIdx.x == 0) next = k0 * (int)gridDim.x + atomicAdd(&sched[1], 1);
     const bool ok = mbar_wait(&bars[st], (unsigned)(k / STAGES) & 1u);
     // FP16NEQ: decode before the barrier, which then also publishes the decoded
     // tile (a thread whose wait gave up decodes stale data that is never used)
@@ -1082,7 +1088,7 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
                                ry0, fout, p);
     __syncthreads();   // every thread is done with stage st
     if (threadIdx.x == 0) {
-      if (dynamic) tile_of[st] = next;
+      if (k + STAGES >= k0) tile_of[st] = next;
       if (next < ntiles) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         issue(next, st);
@@ -1132,7 +1138,7 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
     for (int k = 0;; ++k) {
       const int st = k % STAGES;
       const unsigned ph = (unsigned)(k / STAGES) & 1u;
-      const bool fixed = k < STAGES || !dynamic;
+      const bool fixed = k < k0;
       int t = (int)blockIdx.x + k * (int)gridDim.x;
       if (fixed && t >= ntiles) break;
       if (!__all_sync(0xffffffffu, mbar_wait_or_abort(&full[st], ph, abort))) {
@@ -1147,7 +1153,8 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
       // the tile of this stage's next use; a claim is made now so that its
       // latency overlaps the compute
       int next = t + stride;
-      if (dynamic && threadIdx.x == 0) next = stride + atomicAdd(&sched[1], 1);
+      const bool claim = k + STAGES >= k0;   // the use k + STAGES takes a claimed tile
+      if (claim && threadIdx.x == 0) next = k0 * (int)gridDim.x + atomicAdd(&sched[1], 1);
       int x0, y0, ry0;
       tile_origin(t, x0, y0, ry0);
       const float4* tab = tables(st);
@@ -1157,13 +1164,13 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[st]);
       int pfail = 0;
-      if (threadIdx.x == 0 && (next < ntiles || dynamic)) {
+      if (threadIdx.x == 0 && (next < ntiles || claim)) {
         // refill stage st for use k + STAGES once every warp is done with use k
         if (!mbar_wait_or_abort(&empty[st], ph, abort)) {
           fail();
           pfail = 1;
         } else {
-          if (dynamic) tile_of[st] = next;
+          if (claim) tile_of[st] = next;
           if (next < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             issue(next, st);
@@ -1179,7 +1186,7 @@ __global__ void __launch_bounds__(kThreads, (tma_ctas_per_sm<S, R, STAGES>()))
     if (threadIdx.x == 0)
       for (int u = seen; u < filled; ++u) mbar_wait(&full[u % STAGES], (unsigned)(u / STAGES) & 1u);
   }
-  if (dynamic && threadIdx.x == 0) {
+  if (k0 != kFixedOrder && threadIdx.x == 0) {
     // every claim of this CTA is done; the last CTA out resets the counters
     __threadfence();
     if (atomicAdd(&sched[2], 1) == (int)gridDim.x - 1) {
@@ -1373,22 +1380,38 @@ cudaError_t launch_tiled(const Solver& s, const S* in, S* out, const P2<float>& 
 }
 
 
-// Tiles per CTA from which k_step_tma claims its tiles dynamically.  Measured
-// on the FP32 1024^2 .. 8192^2 cavities: below ~24 tiles per CTA the fixed
-// stride is up to 4% faster, beyond ~50 the claimed order wins (1.47x at 8192^2).
-constexpr int kDynamicTilesPerCta = 24;
+// Tiles per CTA from which k_step_tma claims every tile after the first
+// STAGES.  Measured on the FP32 1024^2 .. 8192^2 cavities: at 27 tiles per CTA
+// (2048^2) the fixed stride is 2% faster, at 108 (4096^2) the claimed order
+// is 1.2x faster and at 8192^2 1.5x.
+constexpr int kClaimAllTilesPerCta = 64;
 
-// Tuning override of that choice: ISLBM_TMA_SCHEDULE=fixed / claimed (unset:
-// automatic).
+// Tuning override of the tile order: ISLBM_TMA_SCHEDULE=fixed / claimed /
+// tail (unset: automatic).
 int tma_schedule_override() {
   static const int v = [] {
     const char* e = std::getenv("ISLBM_TMA_SCHEDULE");
     if (!e) return -1;
     if (std::strcmp(e, "fixed") == 0) return 0;
     if (std::strcmp(e, "claimed") == 0) return 1;
+    if (std::strcmp(e, "tail") == 0) return 2;
     return -1;
   }();
   return v;
+}
+
+// k0 of k_step_tma (the first claimed stage use): claimed throughout on large
+// meshes, the fixed stride below that.  The `tail` order (the fixed stride one
+// tile short of the CTAs' common share, then claimed tiles) was measured
+// slower than the fixed stride at 1024^2 (41.4k against 44.5k MLUPS) and
+// 2048^2, so it is only an option.
+int tma_first_claim(int ntiles, int grid, int stages) {
+  const int per_cta = ntiles / grid;
+  int mode = tma_schedule_override();
+  if (mode < 0) mode = per_cta >= kClaimAllTilesPerCta ? 1 : 0;
+  if (mode == 1) return per_cta >= stages ? stages : kFixedOrder;
+  if (mode == 2) return per_cta - 1 >= stages ? per_cta - 1 : kFixedOrder;
+  return kFixedOrder;
 }
 
 template <typename S, int R, int STAGES>
@@ -1411,11 +1434,10 @@ cudaError_t launch_tma(const Solver& s, int cur, S* out, const P2<float>& p) {
   const int ntiles = ((s.n[0] + kTX - 1) / kTX) * ((step_rows(s) + G::TY - 1) / G::TY);
   const int grid = std::min(ntiles, s.sm_count * blocks_per_sm);
   // claimed tiles pay off once a CTA walks more than a few dozen tiles
-  const int ov = tma_schedule_override();
-  const int dynamic = ov >= 0 ? ov : (ntiles >= kDynamicTilesPerCta * grid ? 1 : 0);
+  const int k0 = tma_first_claim(ntiles, grid, STAGES);
   k_step_tma<S, R, STAGES><<<grid, kThreads, smem, s.stream>>>(
       *reinterpret_cast<const CUtensorMap*>(s.tmap[cur]),
-      *reinterpret_cast<const CUtensorMap*>(s.tmap_m[cur]), out, p, s.derr, dynamic);
+      *reinterpret_cast<const CUtensorMap*>(s.tmap_m[cur]), out, p, s.derr, k0);
   return cudaGetLastError();
 }
 

@@ -1,12 +1,20 @@
 """Tile order of the 2-D TMA step where tiles are claimed from a device counter.
 
 On a 2048^2 mesh the step has 8,192 tiles of 64 x 8 nodes for at most 304
-resident CTAs (152 SMs x 2), more than the 24 tiles per CTA from which the
-launch hands tiles out by a counter instead of a fixed stride.  A tile that is
-skipped, a tile computed from another tile's staged data, or a counter left
-unreset between launches (the last CTA resets it) shows up as an O(1) error:
-the stale buffer holds the state of two steps earlier.
+resident CTAs (152 SMs x 2): 26 per CTA, which the launch hands out at a fixed
+stride by default.  ISLBM_TMA_SCHEDULE=claimed claims every tile after the
+first two from a counter (the default from 64 tiles per CTA), and
+ISLBM_TMA_SCHEDULE=tail takes the first 25 at the fixed stride and claims the
+rest.  A
+tile that is skipped, a tile computed from another tile's staged data, or a
+counter left unreset between launches (the last CTA resets it) shows up as an
+O(1) error: the stale buffer holds the state of two steps earlier.
 """
+import json
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -27,7 +35,7 @@ def _pkg():
     return pkg
 
 
-def test_claimed_tiles_every_population_against_oracle():
+def test_default_tile_order_every_population_against_oracle():
     """Three steps from a far-from-equilibrium random state: all 58.7M
     populations against the FP64 oracle at the FP32 population tolerance."""
     pkg = _pkg()
@@ -47,21 +55,42 @@ def test_claimed_tiles_every_population_against_oracle():
     assert np.abs(gp - gp_ref).max() / np.abs(gp_ref).max() <= 2e-6
 
 
-def test_claimed_tiles_over_many_launches_match_one_tile_per_cta():
-    """70 steps (a captured graph of 64 launches, then 6 single launches) of the
-    claimed order against the kernel that stages one tile per CTA with no tile
-    order at all: the same arithmetic per node, so the fields agree to FP32
-    rounding."""
-    pkg = _pkg()
-    xi = pkg.islbm_mesh_tanh(N, 1.5)
-    out = {}
-    for kernel in ("tma_r2s2", "tiled"):
-        s = pkg.Solver(xi, xi, Ra=1e8, precision="fp32", kernel=kernel)
-        s.set_fields(temperature_noise(s.shape, 1e-6, seed=4))
-        s.step(70)
-        out[kernel] = s.fields()
-        assert s.reduce()["status"] == 0
-        s.close()
-    for k in ("T", "u", "v"):
-        a, b = out["tma_r2s2"][k], out["tiled"][k]
-        assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max(), k
+_SUBPROCESS = r"""
+import json, sys
+import numpy as np
+import paper_2509_01099_gb300 as pkg
+from synthetic import temperature_noise
+xi = pkg.islbm_mesh_tanh(%d, 1.5)
+out = {}
+for kernel in ("tma_r2s2", "tiled"):
+    s = pkg.Solver(xi, xi, Ra=1e8, precision="fp32", kernel=kernel)
+    s.set_fields(temperature_noise(s.shape, 1e-6, seed=4))
+    s.step(70)
+    out[kernel] = s.fields()
+    assert s.reduce()["status"] == 0
+    s.close()
+err = {k: float(np.abs(out["tma_r2s2"][k] - out["tiled"][k]).max() / np.abs(out["tiled"][k]).max())
+       for k in ("T", "u", "v")}
+print(json.dumps(err))
+"""
+
+
+@pytest.mark.parametrize("schedule", ["default", "claimed", "tail"])
+def test_tile_orders_over_many_launches_match_one_tile_per_cta(schedule):
+    """70 steps (a captured graph of 64 launches, then 6 single launches) in
+    each tile order against the kernel that stages one tile per CTA with no
+    tile order at all: the same arithmetic per node, so the fields agree to
+    FP32 rounding.  The order is read once per process, so each runs in a
+    process of its own."""
+    _pkg()
+    env = dict(os.environ)
+    env.pop("ISLBM_TMA_SCHEDULE", None)
+    if schedule != "default":
+        env["ISLBM_TMA_SCHEDULE"] = schedule
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _SUBPROCESS % N], cwd=root, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    err = json.loads(r.stdout.strip().splitlines()[-1])
+    for k, e in err.items():
+        assert e <= 1e-6, (schedule, k, e)
