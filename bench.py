@@ -55,6 +55,9 @@ def parse():
                     help="time every kernel variant and storage type; print one JSON line each")
     ap.add_argument("--steady", action="store_true",
                     help="wall time to a steady Nu: plain, mixed precision, learned warm start")
+    ap.add_argument("--steady-precision", action="store_true",
+                    help="wall time to a steady Nu of single cavities in FP64 (the paper's "
+                         "precision), FP32, FP16NEQ and BF16DEV storage")
     ap.add_argument("--sweep3d", action="store_true", help="time the 3-D step (256^3)")
     ap.add_argument("--convergence", action="store_true",
                     help="Ra=1e6 grid convergence on 257/513/1025 erf meshes (Table 2)")
@@ -432,6 +435,72 @@ def steady(args, pkg, torch):
                       "in [1e6, 1e8] (seed 2)", "criterion": "Nu window means, 100 x 1000 steps, "
                       "tol 2e-4", "Ra": [float(r) for r in ras], "summary": summary,
                       "arms": res}), flush=True)
+
+
+def steady_precision(args, pkg, torch, count=4, tol=2e-4, sample=1000, window=100):
+    """Wall time to a steady Nu by storage precision alone: `count` of the 16
+    held-out Ra (PCG64 seed 2) of the 256^2 tanh cavity (a = 1.5), each run as
+    a single solver from the rest state, one cavity after the other, in FP64
+    (the paper's precision), FP32, FP16NEQ and BF16DEV.  The criterion is the
+    one of islbm_batch_run_to_steady_nu, applied here on the host: window means
+    of Nu over `window` samples `sample` steps apart agreeing to `tol`; the
+    step budget is --max-steps per cavity (default 2M).  Deviations are
+    relative to the FP64 arm and to the FP32 arm."""
+    from synthetic import ra_sweep
+    ras = ra_sweep(16, seed=2)[0][:count]
+    budget = args.max_steps or 2_000_000
+    xi = pkg.islbm_mesh_tanh(256, 1.5)
+    res = {}
+    for prec in ("fp64", "fp32", "fp16neq", "bf16dev"):
+        arm = {"steps": [], "Nu": [], "Re": [], "steady": [], "kernel": None}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for ra in ras:
+            s = pkg.Solver(xi, xi, Ra=float(ra), precision=prec)
+            arm["kernel"] = int(s.info.kernel)
+            prev, acc_nu, acc_re, k, t, done = None, 0.0, 0.0, 0, 0, False
+            nu = re = float("nan")
+            while t + sample <= budget:
+                s.step(sample)
+                t += sample
+                r = s.reduce(check=False)
+                acc_nu += r["Nu"]
+                acc_re += r["Re"]
+                k += 1
+                if k < window:
+                    continue
+                nu, re = acc_nu / window, acc_re / window
+                acc_nu = acc_re = 0.0
+                k = 0
+                if prev is not None and abs(nu - prev) <= tol * abs(nu):
+                    done = True
+                    break
+                prev = nu
+            s.close()
+            arm["steps"].append(t)
+            arm["Nu"].append(nu)
+            arm["Re"].append(re)
+            arm["steady"].append(done)
+        torch.cuda.synchronize()
+        arm["wall_s"] = time.perf_counter() - t0
+        res[prec] = arm
+    out = {"steady_precision": True,
+           "workload": "2-D cavity 256^2 tanh a=1.5, Ra: %d of the 16 held-out (seed 2), single "
+                       "solvers one after the other from rest" % count,
+           "criterion": "Nu window means, %d x %d steps, tol %g; budget %d steps per cavity"
+                        % (window, sample, tol, budget),
+           "Ra": [float(r) for r in ras], "arms": {}}
+    for prec, arm in res.items():
+        row = {"wall_s": arm["wall_s"], "steps_total": int(sum(arm["steps"])),
+               "all_steady": all(arm["steady"]), "kernel": arm["kernel"],
+               "Nu": arm["Nu"], "Re": arm["Re"]}
+        for ref in ("fp64", "fp32"):
+            b = res[ref]
+            row[f"wall_rel_to_{ref}"] = arm["wall_s"] / b["wall_s"]
+            row[f"max_Nu_dev_from_{ref}"] = max(abs(x / y - 1) for x, y in zip(arm["Nu"], b["Nu"]))
+            row[f"max_Re_dev_from_{ref}"] = max(abs(x / y - 1) for x, y in zip(arm["Re"], b["Re"]))
+        out["arms"][prec] = row
+    print(json.dumps(out), flush=True)
 
 
 def steady_lines(pkg, count=4, max_steps=2_000_000):
@@ -1090,6 +1159,9 @@ def main():
         return
     if args.steady:
         steady(args, pkg, torch)
+        return
+    if args.steady_precision:
+        steady_precision(args, pkg, torch)
         return
     if args.sweep3d:
         sweep3d(args, pkg, torch, flush)

@@ -90,3 +90,49 @@ def test_clock_sampler_names_the_gpu_the_rank_runs_on(monkeypatch):
     assert bench.gpu_selector(1) == "7"
     monkeypatch.delenv("CUDA_VISIBLE_DEVICES")
     assert bench.gpu_selector(2) == "2"
+
+
+class _FakeSolver:
+    """Stands in for a solver whose volume-averaged Nu relaxes as 1 + e^(-t/tau)
+    in time steps, with tau set by the storage precision."""
+    TAU = {"fp64": 20_000.0, "fp32": 20_000.0, "fp16neq": 20_000.0, "bf16dev": 2e12}
+
+    def __init__(self, xi_x, xi_y, Ra, precision):
+        import types
+        self.t, self.prec = 0, precision
+        self.info = types.SimpleNamespace(kernel=1 if precision == "fp64" else 4)
+
+    def step(self, n):
+        self.t += n
+
+    def reduce(self, check=True):
+        import math
+        tau = self.TAU[self.prec]
+        # BF16DEV: a slow drift that never settles to the tolerance
+        nu = 1.0 + math.exp(-self.t / tau) if tau < 1e9 else 1.0 + self.t * 1e-8
+        return {"Nu": nu, "Re": 2.0 * nu}
+
+    def close(self):
+        pass
+
+
+def test_steady_precision_host_loop(monkeypatch, capsys):
+    """The host-side Nu-window criterion of --steady-precision: windows of 100
+    samples 1000 steps apart, steady when two window means agree to 2e-4; the
+    budget caps an arm that never settles; deviations are taken against the
+    FP64 and FP32 arms."""
+    import json
+    import types
+    torch = types.SimpleNamespace(cuda=types.SimpleNamespace(synchronize=lambda: None))
+    pkg = types.SimpleNamespace(Solver=_FakeSolver, islbm_mesh_tanh=lambda n, a: None)
+    args = types.SimpleNamespace(max_steps=600_000)
+    bench.steady_precision(args, pkg, torch, count=2)
+    out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    arms = out["arms"]
+    # exp(-t/2e4): the window means (samples 1e3 .. 1e5, 1.01e5 .. 2e5, ...)
+    # are 1 + 0.198, 1 + 1.3e-3, 1 + 9e-6, 1 + 6e-8: the fourth is the first
+    # within 2e-4 of the one before, so each cavity stops after 400k steps
+    assert arms["fp64"]["steps_total"] == 2 * 400_000 and arms["fp64"]["all_steady"]
+    assert arms["fp32"]["max_Nu_dev_from_fp64"] == 0.0
+    assert arms["bf16dev"]["steps_total"] == 2 * 600_000 and not arms["bf16dev"]["all_steady"]
+    assert arms["bf16dev"]["max_Nu_dev_from_fp64"] > 0
