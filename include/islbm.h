@@ -459,6 +459,19 @@ ISLBM_API islbm_status islbm_debug_bounds(int reset, int* flagged);
  * CUDA failure.  Synchronises `stream`; the context stays usable. */
 ISLBM_API islbm_status islbm_selftest_wait_timeout(void* stream);
 
+/* Self-test of the CTA abort flag of the barrier-free pipelined loops (the
+ * paper has no counterpart): in one CTA, warp 0 waits on an mbarrier that
+ * nothing arrives at until the wait limit and then raises the CTA's abort
+ * flag; the other warps make three waits on another such mbarrier, each of
+ * which gives up at its own limit or as soon as the flag is up.
+ * *failed_waits (host) receives the failed waits of warp 1 (3 expected), *ms
+ * (host) their total time in milliseconds (about one wait limit, 1000 ms,
+ * when the flag ends the second and third waits; three limits without it).
+ * Returns ISLBM_ERR_TIMEOUT when warp 0's wait gave up (the expected outcome),
+ * ISLBM_ERR_ARG for a null pointer, ISLBM_ERR_CUDA / ISLBM_ERR_OOM on a CUDA
+ * failure.  Synchronises `stream`; the context stays usable. */
+ISLBM_API islbm_status islbm_selftest_wait_abort(void* stream, int* failed_waits, int* ms);
+
 /* ---- device memory --------------------------------------------------------------
  * Every device allocation of the library (a handle's population buffers,
  * tables, scratch and staging buffers, a batch's work lists, the network

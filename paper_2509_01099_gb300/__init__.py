@@ -10,6 +10,7 @@ from .islbm import (EXPORTS, KERNEL_VARIANTS, KERNELS, LATTICES, MESH_KINDS, PRE
                     islbm_get_populations, islbm_info, islbm_load, islbm_mass, islbm_mesh_erf,
                     islbm_mesh_tanh, islbm_mesh_uniform, islbm_nusselt, islbm_reduce,
                     islbm_reduce_noalloc, islbm_reynolds, islbm_run_to_steady, islbm_save, islbm_selftest_wait_timeout,
+                    islbm_selftest_wait_abort,
                     islbm_set_fields, islbm_set_fields_device, islbm_set_populations,
                     islbm_steady_change, islbm_step, islbm_synchronize, library_path,
                     load_library, islbm_set_row_range, islbm_get_rows, islbm_set_rows,

@@ -37,6 +37,7 @@ EXPORTS = (
     "islbm_batch_tile_rows", "islbm_batch_step", "islbm_batch_synchronize",
     "islbm_batch_run_to_steady", "islbm_batch_run_to_steady_nu", "islbm_average_reset",
     "islbm_average_add", "islbm_average_get", "islbm_debug_bounds", "islbm_selftest_wait_timeout",
+    "islbm_selftest_wait_abort",
     "islbm_cnn_gemm_bf16", "islbm_cnn_im2col", "islbm_cnn_col2im",
     "islbm_cnn_upsample2x", "islbm_cnn_tanh", "islbm_cnn_tanh_back", "islbm_cnn_to_bf16",
     "islbm_cnn_colsum", "islbm_cnn_mse", "islbm_cnn_adam", "islbm_cnn_pack_fields",
@@ -198,6 +199,7 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
         "islbm_batch_synchronize": (i, [h]),
         "islbm_debug_bounds": (i, [i, P(i)]),
         "islbm_selftest_wait_timeout": (i, [vp]),
+        "islbm_selftest_wait_abort": (i, [vp, P(ctypes.c_int), P(ctypes.c_int)]),
         "islbm_average_reset": (i, [h]),
         "islbm_average_add": (i, [h]),
         "islbm_average_get": (i, [h, dp, dp, dp, dp, P(ctypes.c_longlong)]),
@@ -573,6 +575,16 @@ def islbm_selftest_wait_timeout(stream=None) -> int:
     if stream is None:
         stream = _current_stream()
     return load_library().islbm_selftest_wait_timeout(stream)
+
+
+def islbm_selftest_wait_abort(stream=None):
+    """(status, failed waits, ms) of the abort-flag self-test: ISLBM_ERR_TIMEOUT = 6,
+    3 failed waits and about 1000 ms are the expected outcome."""
+    if stream is None:
+        stream = _current_stream()
+    failed, ms = ctypes.c_int(), ctypes.c_int()
+    st = load_library().islbm_selftest_wait_abort(stream, ctypes.byref(failed), ctypes.byref(ms))
+    return st, failed.value, ms.value
 
 
 def islbm_synchronize(h):
